@@ -1,0 +1,362 @@
+#!/usr/bin/env python3
+"""Benchmark: batched FISTA at L1 = L2 = 256 through the C ABI.
+
+Workload (one "step"): a batch of B independent snapshots, each drawn like the
+single-snapshot 256 x 256 workload (32 x 32 half-wavelength array with N = 256
+random elements, 8 off-grid sources with CN(0,1) amplitudes, 10 dB SNR, lam =
+0.05 ||A^H y||_inf computed on the device), solved with T = 1000 FISTA
+iterations: FP64 setup (Lambda, mu, b, lam), the fused FP32 iterations, and the
+FP64 KKT / objective check, all in the library's kernels.
+
+value = B * T * steps / time (instance-iterations per second, all ranks).
+Under torchrun each rank solves its own B snapshots (weak scaling, no
+collective on the data path).
+
+``--impl reference`` times the FP64 dense oracle (the paper's "regular"
+implementation) on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "batched FISTA iters/s at L1=L2=256; time to 1e-4 rel. error vs plain path"
+UNIT = "instance-iterations/s"
+WORKLOAD = dict(M1=32, M2=32, N=256, L1=256, L2=256, K=8, snr_db=10.0, lam_frac=0.05)
+SM_COUNT_NOMINAL = 152
+FP32_LANES_PER_SM = 128
+
+
+def workload_name(B, T):
+    return (f"batched FISTA: {B} snapshots/GPU, 32x32 half-wavelength array, N=256 random elements, "
+            f"256x256 grid, 8 off-grid CN(0,1) sources, 10 dB, lam=0.05*||A^H y||_inf, {T} iterations")
+
+
+def flops_per_inst_iter(L1, L2):
+    """Algorithmic FP32 flops of one iteration on one L1 x L2 grid: a forward and an
+    inverse 2D FFT at 5 L log2 L each, plus 18 L pointwise (real multiplier 2,
+    + mu b 2, soft threshold 8, momentum 6)."""
+    import math
+
+    L = L1 * L2
+    return 10.0 * L * math.log2(L) + 18.0 * L
+
+
+def make_batch(B, first):
+    import synth
+
+    out = []
+    for i in range(first, first + B):
+        s = synth.make_snapshot(20000 + i, WORKLOAD["M1"], WORKLOAD["M2"], WORKLOAD["N"], WORKLOAD["L1"],
+                                WORKLOAD["L2"], WORKLOAD["K"], WORKLOAD["snr_db"])
+        out.append(s)
+    return out
+
+
+# ------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(pw) if pw else None, "samples": len(rows), "reasons": reasons}
+
+
+def gpu_index_for_smi(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids):
+            return ids[local_rank]
+    return str(local_rank)
+
+
+# ------------------------------------------------------------------------------------------
+# CPU baseline: the FP64 dense oracle on a bounded sample
+# ------------------------------------------------------------------------------------------
+
+
+def cpu_oracle_sample(n_inst, iters, first=0):
+    import oracle
+
+    snaps = make_batch(n_inst, first)
+    t0 = time.perf_counter()
+    for s in snaps:
+        A = oracle.dictionary(s.mask, s.M1, s.M2, s.L1, s.L2)
+        lam = WORKLOAD["lam_frac"] * oracle.lambda_max(A, s.y)
+        oracle.fista(A, s.y, lam, iters)
+    dt = time.perf_counter() - t0
+    return n_inst * iters / dt, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    n_inst, iters = 1, 50
+    for _ in range(args.warmup):
+        cpu_oracle_sample(n_inst, iters)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        cpu_oracle_sample(n_inst, iters, first=k)
+    dt = time.perf_counter() - t0
+    value = args.steps * n_inst * iters / dt
+    sample = f"{n_inst} snapshot x {iters} FISTA iterations per step, dense FP64 oracle (setup included)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(args.batch, args.iters), "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def run_gpu(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_2509_13592_gb300 as bccb
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    B, T = args.batch, args.iters
+    snaps = make_batch(B, rank * B)
+    insts = [dict(M1=s.M1, M2=s.M2, L1=s.L1, L2=s.L2, mask=s.mask, y=s.y, lam=WORKLOAD["lam_frac"],
+                  lam_is_frac=True) for s in snaps]
+    stream = torch.cuda.current_stream()
+    solver = bccb.BatchSolver(insts, "fista", stream=stream)
+    y_dev = torch.from_numpy(solver.y_host).cuda()
+    c_dev = torch.empty(solver.total_c, dtype=torch.complex64, device="cuda")
+    bccb.bccb_set_timing(solver.handle, True)
+
+    def step():
+        solver.solve(y_dev, T, c_dev, check=True)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    iterate_ms, setup_ms, check_ms, launches = [], [], [], 0
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(gpu_index_for_smi(local_rank)) as clocks:
+        barrier()
+        start.record(stream)
+        for _ in range(args.steps):
+            step()
+            t = bccb.bccb_last_timing(solver.handle)  # waits for this step's events
+            iterate_ms.append(t["iterate_ms"])
+            setup_ms.append(t["setup_ms"])
+            check_ms.append(t["check_ms"])
+            launches += t["launches"]
+        end.record(stream)
+        barrier()
+    elapsed = start.elapsed_time(end) / 1e3
+    if dist is not None:
+        t_all = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
+        elapsed = float(t_all.item())
+    value = world * B * T * args.steps / elapsed
+    clock = clocks.summary()
+
+    # per-instance check of the last step
+    res = solver.results()
+    kkt_max = float(np.max(res["kkt"]))
+
+    # ---- end to end through the host-buffer entry point (pinned host memory)
+    y_pin = torch.from_numpy(solver.y_host).pin_memory()
+    c_pin = torch.empty(solver.total_c, dtype=torch.complex64).pin_memory()
+    bccb.bccb_set_timing(solver.handle, False)
+    bccb.bccb_batch_solve_host_ptr(solver.handle, y_pin.data_ptr(), T, c_pin.data_ptr(), True)  # warm
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        bccb.bccb_batch_solve_host_ptr(solver.handle, y_pin.data_ptr(), T, c_pin.data_ptr(), True)
+    barrier()
+    e2e_elapsed = time.perf_counter() - t0
+    if dist is not None:
+        t_all = torch.tensor([e2e_elapsed], device="cuda")
+        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
+        e2e_elapsed = float(t_all.item())
+    e2e_value = world * B * T * args.steps / e2e_elapsed
+
+    # ---- iterations (and time) until every sampled instance is within 1e-4 of its
+    # T-iteration result: FISTA's iterates do not depend on T, so a solve with t
+    # iterations gives iterate t of the plain path.
+    ttt = None
+    if rank == 0 and not args.no_ttt:
+        sub = insts[: min(64, B)]
+        sub_solver = bccb.BatchSolver(sub, "fista", stream=stream)
+        ys = torch.from_numpy(sub_solver.y_host).cuda()
+        ref = torch.empty(sub_solver.total_c, dtype=torch.complex64, device="cuda")
+        sub_solver.solve(ys, T, ref, check=False)
+        ref_np = sub_solver.unpack(ref.cpu().numpy())
+        cur = torch.empty_like(ref)
+        t_star = None
+        for t in range(10, T + 1, 10):
+            sub_solver.solve(ys, t, cur, check=False)
+            cur_np = sub_solver.unpack(cur.cpu().numpy())
+            worst = max(float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)) for a, b in zip(cur_np, ref_np))
+            if worst <= 1e-4:
+                t_star = t
+                break
+        sub_solver.close()
+        per_iter_ms = statistics.median(iterate_ms) / T
+        ttt = {"iters": t_star, "sampled_instances": len(sub), "reference_iters": T,
+               "time_ms_full_batch": None if t_star is None else t_star * per_iter_ms}
+
+    if rank == 0:
+        peaks = load_peaks()
+        props = torch.cuda.get_device_properties(local_rank)
+        sm_count = props.multi_processor_count
+        sm_max = peaks.get("sm_max_mhz", 2070.0)
+        peak_tflops = sm_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        flops_launch = flops_per_inst_iter(256, 256) * B * T
+        it_ms = statistics.mean(iterate_ms)
+        achieved = flops_launch / (it_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": None,
+                "kernel": "fused_solve_kernel<256,256,FISTA> (one launch per step)",
+                "peak_note": f"FP32: {sm_count} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_max:.0f} MHz",
+                "frac_at_median_clock": (achieved / (sm_count * FP32_LANES_PER_SM * 2 * clock["sm_mhz"] * 1e6 / 1e12)
+                                         if clock.get("sm_mhz") else None)}
+        if args.traffic_bytes is not None:
+            roof["traffic"] = args.traffic_bytes
+        cpu = None
+        if not args.no_cpu:
+            n_cpu, it_cpu = 2, 300
+            v, dt = cpu_oracle_sample(n_cpu, it_cpu, first=10**6)
+            cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"{n_cpu} snapshots x {it_cpu} FISTA iterations of the same workload, dense FP64 "
+                             f"oracle with setup ({dt:.1f} s)"}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(B, T), "batch_per_gpu": B, "L1": 256, "L2": 256, "iters": T,
+                       "l2_policy": f"inputs larger than L2: {solver.total_c * 8 * 7 / 2**30:.1f} GiB resident per GPU",
+                       "parallelism": f"instances sharded over {world} GPU(s)"},
+            "phases_ms": {"setup": statistics.mean(setup_ms), "iterate": it_ms, "check": statistics.mean(check_ms)},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(solver.y_host.nbytes),
+                    "d2h_bytes_per_step": int(solver.total_c * 8)},
+            "gpu_launches": launches,
+            "clocks": clock,
+            "kkt_max": kkt_max,
+            "time_to_1e-4": ttt,
+        }
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=4096, help="snapshots per GPU")
+    ap.add_argument("--iters", type=int, default=1000)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-1e-4 measurement")
+    ap.add_argument("--traffic-bytes", type=float, default=None,
+                    help="DRAM bytes per launch of the fused kernel from an ncu capture")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_gpu(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,146 @@
+/*
+ * bccb.h -- C ABI of the GB300 BCCB sparse-recovery solver.
+ *
+ * Solves the single-snapshot 2D harmonic-recovery LASSO of arXiv 2509.13592,
+ *     minimise_c  1/2 ||y - D_s c||_2^2 + lam ||c||_1       (eq:lasso_objective, Section II-A)
+ * with ISTA (eq:ista), FISTA (eq:fista) or ADMM (eq:admm).  The sparse array's
+ * elements sit on a half-wavelength grid and the harmonic grids are uniform
+ * (eq:uniform_grid, gamma = 1/2), so D_s^H D_s is block-circulant with circulant
+ * blocks (eq:bccb_sum) and every Gram product is IFFT2(Lambda . FFT2(x)) on the
+ * L1 x L2 grid (eq:Rc, Section III-B).  All iterations run in hand-written
+ * sm_103a kernels; nothing falls back to the CPU.
+ *
+ * Notation: lam is the paper's tau (the LASSO weight), N the number of kept array
+ * elements (the paper's M), L1 x L2 the harmonic grid.
+ *
+ * Layouts
+ *   mask   uint8, M1*M2 entries, mask[m1 + m2*M1] != 0 keeps URA element (m1, m2)
+ *          (the subsampling matrix Psi, Section II-A).  Host memory.
+ *   y      complex64 (interleaved float re, im), N entries: the kept elements in
+ *          ascending order of m1 + m2*M1 (the rows of Psi).
+ *   c      complex64, L1*L2 entries stored as an L2 x L1 row-major grid: entry
+ *          l1 + l2*L1 is the amplitude at harmonics (f_{1,l1}, f_{2,l2}) with
+ *          f_{i,l} = -1/2 + l/L_i (Section II-A: column l1 + l2 L1 of D).
+ * Supported grids: L1, L2 powers of two in [16, 256]; M1, M2 >= 1 (masks wider
+ * than the grid fold, which the BCCB structure allows).
+ *
+ * Conventions
+ *   * Every call returns a status (BCCB_OK = 0).  No exception crosses the ABI and
+ *     no kernel traps; bccb_last_error() gives a message for the last failure.
+ *   * Device pointers are caller-owned and must stay valid until the stream work
+ *     finishes; the solver owns its internal buffers (Lambda, mu*b or d,
+ *     multipliers, FP64 workspace).
+ *   * All device work is queued on the solver's stream (cudaStream_t passed as
+ *     void*, NULL = legacy default stream).  Calls that return host values
+ *     (bccb_batch_results, bccb_solve's kkt/objective, *_host) synchronise that
+ *     stream.
+ *   * Not thread-safe per solver; distinct solvers may be used from distinct threads.
+ */
+#ifndef BCCB_H
+#define BCCB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bccb_solver* bccb_solver_t;
+
+/* Algorithms (Section II-B). */
+enum { BCCB_ISTA = 0, BCCB_FISTA = 1, BCCB_ADMM = 2 };
+
+/* Status codes. */
+enum {
+  BCCB_OK = 0,
+  BCCB_ERR_INVALID_ARG = 1, /* null pointer, bad size, empty mask, rho <= 0, ... */
+  BCCB_ERR_UNSUPPORTED = 2, /* grid size outside the supported set */
+  BCCB_ERR_CUDA = 3,        /* a CUDA call failed; see bccb_last_error() */
+  BCCB_ERR_KKT = 4,         /* reserved: result returned but the KKT check failed */
+  BCCB_ERR_TIMEOUT = 5      /* reserved: a bounded device wait expired */
+};
+
+/* One instance of a batch.  Offsets let the caller pack many instances into one
+ * mask buffer (bytes), one y buffer and one c buffer (complex elements). */
+typedef struct {
+  int32_t M1, M2;      /* URA size (Section II-A) */
+  int32_t L1, L2;      /* harmonic grid lengths (powers of two, 16..256) */
+  int64_t mask_off;    /* byte offset of this instance's M1*M2 mask in masks_host */
+  int64_t y_off;       /* complex64 offset of this instance's N measurements */
+  int64_t c_off;       /* complex64 offset of this instance's L1*L2 solution */
+  double lam;          /* LASSO weight, or a fraction of ||A^H y||_inf if lam_is_frac */
+  int32_t lam_is_frac; /* 0: lam is absolute; 1: lam := lam * ||A^H y||_inf per solve */
+  int32_t reserved;    /* must be 0 */
+} bccb_inst_t;
+
+/* Create a solver for a batch of n independent instances that share one algorithm
+ * (and, for ADMM, one rho > 0; eq:admm).  Copies the masks and instance table to
+ * the device; allocates all internal buffers.  Does not launch the solve.
+ * Errors: INVALID_ARG (n < 1, null pointers, empty mask, bad algo/rho,
+ * reserved != 0), UNSUPPORTED (grid size), CUDA. */
+int bccb_batch_create(bccb_solver_t* out, const bccb_inst_t* insts, int n, const uint8_t* masks_host,
+                      int algo, double rho, void* cuda_stream);
+
+/* Run the whole hot path for every instance on the solver's stream:
+ *   setup (FP64): Lambda = FFT2 of the Gram's first column (eq:lambda),
+ *                 mu = 1/max Lambda (eq:ista), b = A^H y, lam, the FP32 Fourier
+ *                 multiplier and the constant term mu*b (ISTA/FISTA) or
+ *                 d = (G + rho I)^{-1} b (ADMM, "can be precomputed");
+ *   iterations (FP32): `iters` fused ISTA/FISTA/ADMM iterations, each one FFT2,
+ *                 multiply, IFFT2 and the pointwise update (eq:ista/fista/admm, eq:Rc);
+ *   check (FP64, if check != 0): relative KKT residual and objective per instance.
+ * y_dev: packed complex64 measurements (device).  c0_dev: nullable warm start
+ * (complex64, same packing as c_out_dev; ADMM: z^(0)).  c_out_dev: packed complex64
+ * results: c^(T) for ISTA/FISTA, z^(T) for ADMM.  aux_out_dev: nullable; ADMM
+ * writes c^(T) there.  Asynchronous.  Errors: INVALID_ARG (null y/c_out,
+ * iters < 1), CUDA. */
+int bccb_batch_solve(bccb_solver_t s, const void* y_dev, int iters, const void* c0_dev, void* c_out_dev,
+                     void* aux_out_dev, int check);
+
+/* bccb_batch_solve with HOST buffers: copies y to the device, solves, copies c
+ * back; synchronises.  y_host / c_out_host use the same packing as above. */
+int bccb_batch_solve_host(bccb_solver_t s, const void* y_host, int iters, void* c_out_host, int check);
+
+/* Per-instance scalars of the last solve, copied to host arrays of length n (each
+ * nullable): relative KKT residual max_i viol_i / lam (viol = (|r_i| - lam)_+ off
+ * the support, |r_i - lam c_i/|c_i|| on it, r = A^H(y - A c)), objective
+ * 1/2||y - A c||^2 + lam||c||_1, the lam used and mu.  Synchronises. */
+int bccb_batch_results(bccb_solver_t s, double* kkt, double* obj, double* lam, double* mu);
+
+/* Copy an internal per-instance grid of the last solve (device to device), packed
+ * like c_out (instance i at its c_off).  what: 0 = Lambda (float64, real);
+ * 1 = b = A^H y (complex128); 2 = the FP32 Fourier multiplier (float32, includes
+ * 1/(L1 L2)); 3 = the FP32 constant term mu*b or d (complex64).  Asynchronous. */
+int bccb_batch_get(bccb_solver_t s, int what, void* dst_dev);
+
+/* Single-instance convenience: a batch of one (c_off = y_off = 0). */
+int bccb_create(bccb_solver_t* out, int M1, int M2, const uint8_t* mask_host, int L1, int L2, int algo,
+                double rho, void* cuda_stream);
+/* Solve one instance with LASSO weight lam (absolute, or a fraction of
+ * ||A^H y||_inf if lam_is_frac).  kkt_out / obj_out nullable; when either is
+ * given the FP64 check runs and the call synchronises. */
+int bccb_solve(bccb_solver_t s, const void* y_dev, double lam, int lam_is_frac, int iters, const void* c0_dev,
+               void* c_out_dev, void* aux_out_dev, double* kkt_out, double* obj_out);
+
+/* Phase timing of bccb_batch_solve, for profiling.  bccb_set_timing(s, 1) makes
+ * every later solve record CUDA events on the solver's stream around its three
+ * phases; bccb_last_timing synchronises and returns the last solve's setup,
+ * iteration and check durations in milliseconds (0 when timing is off) and the
+ * number of kernels that solve launched (always counted). */
+int bccb_set_timing(bccb_solver_t s, int enable);
+int bccb_last_timing(bccb_solver_t s, float* setup_ms, float* iterate_ms, float* check_ms, int64_t* launches);
+
+/* Number of instances, and the (L1, L2, N) of instance i. */
+int bccb_batch_size(bccb_solver_t s, int* n);
+int bccb_instance_shape(bccb_solver_t s, int i, int* L1, int* L2, int* N);
+
+int bccb_destroy(bccb_solver_t s);
+const char* bccb_status_string(int status);
+/* Message for the solver's last failure ("" if none); s may be NULL for create errors. */
+const char* bccb_last_error(bccb_solver_t s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BCCB_H */

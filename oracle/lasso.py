@@ -96,25 +96,45 @@ def lambda_max(A: np.ndarray, y: np.ndarray) -> float:
     return float(np.max(np.abs(adjoint_measurements(A, y))))
 
 
+class _Gram:
+    """A^H A x as two dense matrix-vector products (the paper's "regular" O(L^2)
+    product); A^H is formed once."""
+
+    def __init__(self, A):
+        self.A = A
+        self.Ah = np.ascontiguousarray(A.conj().T)
+
+    def __call__(self, x):
+        return self.Ah @ (self.A @ x)
+
+
 def _gram_apply(A: np.ndarray, x: np.ndarray) -> np.ndarray:
-    # A^H A x as two dense products (the paper's "regular" O(L^2) product).
     return A.conj().T @ (A @ x)
 
 
-def ista(A, y, lam, iters, mu=None, c0=None, history=False):
+def ista(A, y, lam, iters, mu=None, c0=None, history=False, pre=False):
     """ISTA (eq:ista): c^(t+1) = S_{mu lam}((I - mu A^H A) c^(t) + mu A^H y).
 
-    Returns c^(T); with ``history`` also the list [c^(0), ..., c^(T)].
+    Returns c^(T); with ``history`` also the list [c^(0), ..., c^(T)]; with ``pre``
+    also the last soft-threshold argument u^(T) and the threshold mu*lam.
     """
     mu = step_size(A) if mu is None else float(mu)
+    gram = _Gram(A)
     b = adjoint_measurements(A, y)
     c = np.zeros(A.shape[1], np.complex128) if c0 is None else np.array(c0, np.complex128)
     hist = [c.copy()] if history else None
+    u = c
     for _ in range(iters):
-        c = soft_threshold(c - mu * _gram_apply(A, c) + mu * b, mu * lam)
+        u = c - mu * gram(c) + mu * b
+        c = soft_threshold(u, mu * lam)
         if history:
             hist.append(c.copy())
-    return (c, hist) if history else c
+    out = (c,)
+    if history:
+        out += (hist,)
+    if pre:
+        out += (u, mu * lam)
+    return out if len(out) > 1 else c
 
 
 def fista_momentum(iters: int) -> np.ndarray:
@@ -129,28 +149,37 @@ def fista_momentum(iters: int) -> np.ndarray:
     return beta
 
 
-def fista(A, y, lam, iters, mu=None, c0=None, history=False):
+def fista(A, y, lam, iters, mu=None, c0=None, history=False, pre=False):
     """FISTA (eq:fista).
 
     z^(1) = c^(0); for t = 1..T:
       c^(t)     = S_{mu lam}((I - mu A^H A) z^(t) + mu A^H y)
       z^(t+1)   = c^(t) + beta_t (c^(t) - c^(t-1)).
-    T iterations are T Gram products.  Returns c^(T) (and the list of c^(t)).
+    T iterations are T Gram products.  Returns c^(T) (and the list of c^(t); with
+    ``pre`` also the last soft-threshold argument and the threshold mu*lam).
     """
     mu = step_size(A) if mu is None else float(mu)
+    gram = _Gram(A)
     b = adjoint_measurements(A, y)
     c_prev = np.zeros(A.shape[1], np.complex128) if c0 is None else np.array(c0, np.complex128)
     z = c_prev.copy()
     beta = fista_momentum(iters)
     hist = [c_prev.copy()] if history else None
     c = c_prev
+    u = z
     for t in range(iters):
-        c = soft_threshold(z - mu * _gram_apply(A, z) + mu * b, mu * lam)
+        u = z - mu * gram(z) + mu * b
+        c = soft_threshold(u, mu * lam)
         z = c + beta[t] * (c - c_prev)
         c_prev = c
         if history:
             hist.append(c.copy())
-    return (c, hist) if history else c
+    out = (c,)
+    if history:
+        out += (hist,)
+    if pre:
+        out += (u, mu * lam)
+    return out if len(out) > 1 else c
 
 
 class _AdmmInverse:
@@ -159,6 +188,7 @@ class _AdmmInverse:
 
     def __init__(self, A, rho):
         self.A = A
+        self.Ah = np.ascontiguousarray(A.conj().T)
         self.rho = float(rho)
         K = A @ A.conj().T
         K[np.diag_indices_from(K)] += self.rho
@@ -166,7 +196,7 @@ class _AdmmInverse:
 
     def __call__(self, w):
         Aw = self.A @ w
-        return (w - self.A.conj().T @ scipy.linalg.cho_solve(self.factor, Aw)) / self.rho
+        return (w - self.Ah @ scipy.linalg.cho_solve(self.factor, Aw)) / self.rho
 
 
 def admm_c_update(A, rho):
@@ -174,14 +204,15 @@ def admm_c_update(A, rho):
     return _AdmmInverse(A, rho)
 
 
-def admm(A, y, lam, rho, iters, z0=None, v0=None, history=False):
+def admm(A, y, lam, rho, iters, z0=None, v0=None, history=False, pre=False):
     """ADMM (eq:admm) with the precomputed term d = (A^H A + rho I)^{-1} A^H y:
 
       c^(t+1) = d + rho (A^H A + rho I)^{-1} (z^(t) - v^(t))
       z^(t+1) = S_{lam/rho}(c^(t+1) + v^(t))
       v^(t+1) = v^(t) + c^(t+1) - z^(t+1)
 
-    Returns (z^(T), c^(T), v^(T)); with ``history`` also the list of z^(t).
+    Returns (z^(T), c^(T), v^(T)); with ``history`` also the list of z^(t); with
+    ``pre`` also the last soft-threshold argument c^(T) + v^(T-1) and lam/rho.
     """
     inv = _AdmmInverse(A, rho)
     rho = float(rho)
@@ -191,15 +222,21 @@ def admm(A, y, lam, rho, iters, z0=None, v0=None, history=False):
     v = np.zeros(L, np.complex128) if v0 is None else np.array(v0, np.complex128)
     c = np.zeros(L, np.complex128)
     hist = [z.copy()] if history else None
+    u = z
     for _ in range(iters):
         c = d + rho * inv(z - v)
-        z_new = soft_threshold(c + v, lam / rho)
+        u = c + v
+        z_new = soft_threshold(u, lam / rho)
         v = v + c - z_new
         z = z_new
         if history:
             hist.append(z.copy())
     out = (z, c, v)
-    return (out, hist) if history else out
+    if history:
+        out = (out, hist)
+    if pre:
+        out = out + (u, lam / rho)
+    return out
 
 
 # ------------------------------------------------------------------------------------------
@@ -277,12 +314,13 @@ def unrolled_forward(A, y, mu, theta, save=False):
     b = adjoint_measurements(A, y)
     beta = fista_momentum(K)
     L = A.shape[1]
+    gram = _Gram(A)
     c_prev = np.zeros(L, np.complex128)
     z = c_prev.copy()
     zs, us = [], []
     c = c_prev
     for k in range(K):
-        u = z - mu[k] * (_gram_apply(A, z) - b)
+        u = z - mu[k] * (gram(z) - b)
         c = soft_threshold(u, theta[k])
         if save:
             zs.append(z.copy())
@@ -309,6 +347,7 @@ def unrolled_backward(A, y, mu, theta, grad_c):
     b = adjoint_measurements(A, y)
     beta = fista_momentum(K)
     _, zs, us = unrolled_forward(A, y, mu, theta, save=True)
+    gram = _Gram(A)
     L = A.shape[1]
     d_mu = np.zeros(K)
     d_th = np.zeros(K)
@@ -323,9 +362,9 @@ def unrolled_backward(A, y, mu, theta, grad_c):
         proj = np.real(np.conj(g_c[act]) * u[act])
         g_u[act] = s * g_c[act] + (theta[k] / mag[act] ** 3) * proj * u[act]
         d_th[k] = -float(np.sum(proj / mag[act]))
-        Gz = _gram_apply(A, zs[k])
+        Gz = gram(zs[k])
         d_mu[k] = float(np.real(np.vdot(g_u, b - Gz)))
-        g_z = g_u - mu[k] * _gram_apply(A, g_u)
+        g_z = g_u - mu[k] * gram(g_u)
         # z_k = (1 + beta_(k-1)) c_(k-1) - beta_(k-1) c_(k-2), with z_1 = c_0 = 0 constant.
         if k > 0:
             bk = beta[k - 1]

@@ -1,0 +1,253 @@
+"""Python binding of ``libbccb.so`` (the C ABI declared in include/bccb.h).
+
+Argument marshalling only: every step of the solve runs in the library's CUDA
+kernels.  PyTorch supplies device memory and the CUDA stream.  Importing this
+package fails loudly when the library has not been built; there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbccb.so")
+
+ISTA, FISTA, ADMM = 0, 1, 2
+ALGOS = {"ista": ISTA, "fista": FISTA, "admm": ADMM}
+OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_KKT, ERR_TIMEOUT = range(6)
+GET_LAMBDA, GET_B, GET_MULT, GET_CTERM = 0, 1, 2, 3
+
+
+class BccbError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(msg)
+        self.status = status
+
+
+class bccb_inst_t(ctypes.Structure):
+    _fields_ = [
+        ("M1", ctypes.c_int32), ("M2", ctypes.c_int32), ("L1", ctypes.c_int32), ("L2", ctypes.c_int32),
+        ("mask_off", ctypes.c_int64), ("y_off", ctypes.c_int64), ("c_off", ctypes.c_int64),
+        ("lam", ctypes.c_double), ("lam_is_frac", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build it with `python -m paper_2509_13592_gb300.build` "
+            "(nvcc, sm_103a). There is no CPU fallback.")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    P = ctypes.POINTER
+    lib.bccb_batch_create.argtypes = [P(vp), P(bccb_inst_t), i32, vp, i32, dbl, vp]
+    lib.bccb_batch_solve.argtypes = [vp, vp, i32, vp, vp, vp, i32]
+    lib.bccb_batch_solve_host.argtypes = [vp, vp, i32, vp, i32]
+    lib.bccb_batch_results.argtypes = [vp, vp, vp, vp, vp]
+    lib.bccb_batch_get.argtypes = [vp, i32, vp]
+    lib.bccb_create.argtypes = [P(vp), i32, i32, vp, i32, i32, i32, dbl, vp]
+    lib.bccb_solve.argtypes = [vp, vp, dbl, i32, i32, vp, vp, vp, P(dbl), P(dbl)]
+    lib.bccb_set_timing.argtypes = [vp, i32]
+    lib.bccb_last_timing.argtypes = [vp, P(ctypes.c_float), P(ctypes.c_float), P(ctypes.c_float),
+                                     P(ctypes.c_int64)]
+    lib.bccb_batch_size.argtypes = [vp, P(i32)]
+    lib.bccb_instance_shape.argtypes = [vp, i32, P(i32), P(i32), P(i32)]
+    lib.bccb_destroy.argtypes = [vp]
+    lib.bccb_status_string.argtypes = [i32]
+    lib.bccb_status_string.restype = ctypes.c_char_p
+    lib.bccb_last_error.argtypes = [vp]
+    lib.bccb_last_error.restype = ctypes.c_char_p
+    for name in ("bccb_batch_create", "bccb_batch_solve", "bccb_batch_solve_host", "bccb_batch_results",
+                 "bccb_batch_get", "bccb_create", "bccb_solve", "bccb_batch_size", "bccb_instance_shape",
+                 "bccb_destroy", "bccb_set_timing", "bccb_last_timing"):
+        getattr(lib, name).restype = i32
+    return lib
+
+
+_lib = _load()
+
+
+def _raise(status: int, handle) -> None:
+    if status != OK:
+        msg = _lib.bccb_last_error(handle).decode(errors="replace")
+        what = _lib.bccb_status_string(status).decode()
+        raise BccbError(status, f"{what}: {msg}")
+
+
+def _ptr(t) -> Optional[int]:
+    """Device pointer of a torch tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+# ------------------------------------------------------------------------------------------
+# thin wrappers with the C names
+# ------------------------------------------------------------------------------------------
+
+
+def bccb_batch_create(insts: Sequence[bccb_inst_t], masks_host: np.ndarray, algo: int, rho: float = 1.0,
+                      stream=None) -> int:
+    arr = (bccb_inst_t * len(insts))(*insts)
+    masks = np.ascontiguousarray(masks_host, dtype=np.uint8)
+    h = ctypes.c_void_p()
+    st = _lib.bccb_batch_create(ctypes.byref(h), arr, len(insts), masks.ctypes.data_as(ctypes.c_void_p),
+                                int(algo), float(rho), _stream(stream))
+    _raise(st, None)
+    return h.value
+
+
+def bccb_batch_solve(h: int, y_dev, iters: int, c0_dev, c_out_dev, aux_out_dev=None, check: bool = True) -> None:
+    _raise(_lib.bccb_batch_solve(h, _ptr(y_dev), int(iters), _ptr(c0_dev), _ptr(c_out_dev), _ptr(aux_out_dev),
+                                 1 if check else 0), h)
+
+
+def bccb_batch_solve_host(h: int, y_host: np.ndarray, iters: int, c_out_host: np.ndarray, check: bool = True) -> None:
+    for a in (y_host, c_out_host):
+        if not (isinstance(a, np.ndarray) and a.flags.c_contiguous and a.dtype == np.complex64):
+            raise ValueError("host buffers must be C-contiguous complex64 numpy arrays")
+    _raise(_lib.bccb_batch_solve_host(h, y_host.ctypes.data_as(ctypes.c_void_p), int(iters),
+                                      c_out_host.ctypes.data_as(ctypes.c_void_p), 1 if check else 0), h)
+
+
+def bccb_batch_results(h: int, n: int):
+    kkt, obj, lam, mu = (np.zeros(n) for _ in range(4))
+    vp = ctypes.c_void_p
+    _raise(_lib.bccb_batch_results(h, kkt.ctypes.data_as(vp), obj.ctypes.data_as(vp), lam.ctypes.data_as(vp),
+                                   mu.ctypes.data_as(vp)), h)
+    return {"kkt": kkt, "objective": obj, "lam": lam, "mu": mu}
+
+
+def bccb_batch_get(h: int, what: int, dst_dev) -> None:
+    _raise(_lib.bccb_batch_get(h, int(what), _ptr(dst_dev)), h)
+
+
+def bccb_create(M1: int, M2: int, mask_host: np.ndarray, L1: int, L2: int, algo: int, rho: float = 1.0,
+                stream=None) -> int:
+    m = np.ascontiguousarray(mask_host, dtype=np.uint8).reshape(-1)
+    if m.size != M1 * M2:
+        raise ValueError("mask must have M1*M2 entries")
+    h = ctypes.c_void_p()
+    _raise(_lib.bccb_create(ctypes.byref(h), int(M1), int(M2), m.ctypes.data_as(ctypes.c_void_p), int(L1),
+                            int(L2), int(algo), float(rho), _stream(stream)), None)
+    return h.value
+
+
+def bccb_solve(h: int, y_dev, lam: float, lam_is_frac: bool, iters: int, c0_dev, c_out_dev, aux_out_dev=None,
+               check: bool = True):
+    kkt, obj = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    st = _lib.bccb_solve(h, _ptr(y_dev), float(lam), 1 if lam_is_frac else 0, int(iters), _ptr(c0_dev),
+                         _ptr(c_out_dev), _ptr(aux_out_dev), ctypes.byref(kkt) if check else None,
+                         ctypes.byref(obj) if check else None)
+    _raise(st, h)
+    return (kkt.value, obj.value) if check else None
+
+
+def bccb_set_timing(h: int, enable: bool) -> None:
+    _raise(_lib.bccb_set_timing(h, 1 if enable else 0), h)
+
+
+def bccb_last_timing(h: int):
+    f = [ctypes.c_float(0.0) for _ in range(3)]
+    n = ctypes.c_int64(0)
+    _raise(_lib.bccb_last_timing(h, ctypes.byref(f[0]), ctypes.byref(f[1]), ctypes.byref(f[2]),
+                                 ctypes.byref(n)), h)
+    return {"setup_ms": f[0].value, "iterate_ms": f[1].value, "check_ms": f[2].value, "launches": n.value}
+
+
+def bccb_batch_solve_host_ptr(h: int, y_host_ptr: int, iters: int, c_out_host_ptr: int, check: bool = True) -> None:
+    """Host-buffer entry point on raw host pointers (e.g. pinned torch CPU tensors)."""
+    _raise(_lib.bccb_batch_solve_host(h, y_host_ptr, int(iters), c_out_host_ptr, 1 if check else 0), h)
+
+
+def bccb_destroy(h: int) -> None:
+    _lib.bccb_destroy(h)
+
+
+def bccb_status_string(status: int) -> str:
+    return _lib.bccb_status_string(int(status)).decode()
+
+
+# ------------------------------------------------------------------------------------------
+# packing helper and a small owner object (still marshalling only)
+# ------------------------------------------------------------------------------------------
+
+
+def pack(instances):
+    """Pack instances given as dicts with keys M1, M2, L1, L2, mask (uint8, M1*M2),
+    y (complex, N), lam, lam_is_frac into (inst table, masks, y complex64, total c).
+
+    Instance i's measurements start at y_off = sum of previous N; its solution at
+    c_off = sum of previous L1*L2.
+    """
+    insts, masks, ys = [], [], []
+    m_off = y_off = c_off = 0
+    for d in instances:
+        mask = np.ascontiguousarray(d["mask"], dtype=np.uint8).reshape(-1)
+        y = np.asarray(d["y"]).reshape(-1)
+        q = bccb_inst_t(d["M1"], d["M2"], d["L1"], d["L2"], m_off, y_off, c_off, float(d["lam"]),
+                        1 if d.get("lam_is_frac", False) else 0, 0)
+        insts.append(q)
+        masks.append(mask)
+        ys.append(y.astype(np.complex64))
+        m_off += mask.size
+        y_off += y.size
+        c_off += d["L1"] * d["L2"]
+    return insts, np.concatenate(masks), np.concatenate(ys), c_off
+
+
+class BatchSolver:
+    """Owns one solver handle.  ``instances`` as for :func:`pack`."""
+
+    def __init__(self, instances, algo="fista", rho: float = 1.0, stream=None):
+        self.algo = ALGOS[algo] if isinstance(algo, str) else int(algo)
+        self.insts, self.masks, self.y_host, self.total_c = pack(instances)
+        self.n = len(self.insts)
+        self.offsets = [(q.c_off, q.L1, q.L2) for q in self.insts]
+        self.handle = bccb_batch_create(self.insts, self.masks, self.algo, rho, stream)
+
+    def solve(self, y_dev, iters, c_out, c0=None, aux_out=None, check=True):
+        bccb_batch_solve(self.handle, y_dev, iters, c0, c_out, aux_out, check)
+        return c_out
+
+    def solve_host(self, y_host, iters, c_out_host, check=True):
+        bccb_batch_solve_host(self.handle, y_host, iters, c_out_host, check)
+        return c_out_host
+
+    def results(self):
+        return bccb_batch_results(self.handle, self.n)
+
+    def get(self, what, dst_dev):
+        bccb_batch_get(self.handle, what, dst_dev)
+        return dst_dev
+
+    def unpack(self, flat: np.ndarray):
+        """Split a packed solution (numpy, complex) into per-instance (L2, L1) grids."""
+        return [flat[o:o + L1 * L2].reshape(L2, L1) for (o, L1, L2) in self.offsets]
+
+    def close(self):
+        if self.handle:
+            bccb_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,365 @@
+// C-ABI implementation: argument checks, device buffers, launch sequence.
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "bccb.h"
+#include "solver.h"
+
+using bccb::FusedArgs;
+using bccb::FusedEntry;
+using bccb::FusedInst;
+using bccb::InstDesc;
+using bccb::InstParams;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+int fail(bccb_solver* s, int code, const std::string& msg) {
+  if (s)
+    s->last_error = msg;
+  else
+    g_create_error = msg;
+  return code;
+}
+
+#define BCCB_CUDA(s, expr)                                                                   \
+  do {                                                                                       \
+    cudaError_t e_ = (expr);                                                                 \
+    if (e_ != cudaSuccess) return fail((s), BCCB_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  if (count == 0) count = 1;
+  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+void release(bccb_solver* s) {
+  void* ptrs[] = {s->d_desc, s->d_mask_idx, s->d_lam64, s->d_b64,  s->d_w64,    s->d_mult,    s->d_cterm,
+                  s->d_par,  s->d_fused,    s->d_ids,   s->d_beta, s->d_kkt,    s->d_obj,     s->d_red,
+                  s->d_tw32, s->d_tw64,     s->d_y_stage, s->d_c_stage};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bccb_status_string(int status) {
+  switch (status) {
+    case BCCB_OK: return "ok";
+    case BCCB_ERR_INVALID_ARG: return "invalid argument";
+    case BCCB_ERR_UNSUPPORTED: return "unsupported size";
+    case BCCB_ERR_CUDA: return "CUDA error";
+    case BCCB_ERR_KKT: return "KKT check failed";
+    case BCCB_ERR_TIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+const char* bccb_last_error(bccb_solver_t s) { return s ? s->last_error.c_str() : g_create_error.c_str(); }
+
+int bccb_batch_create(bccb_solver_t* out, const bccb_inst_t* insts, int n, const uint8_t* masks_host, int algo,
+                      double rho, void* cuda_stream) {
+  g_create_error.clear();
+  if (!out) return fail(nullptr, BCCB_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!insts || !masks_host || n < 1) return fail(nullptr, BCCB_ERR_INVALID_ARG, "need n >= 1 instances and masks");
+  if (algo != BCCB_ISTA && algo != BCCB_FISTA && algo != BCCB_ADMM)
+    return fail(nullptr, BCCB_ERR_INVALID_ARG, "algo must be ISTA, FISTA or ADMM");
+  if (algo == BCCB_ADMM && !(rho > 0.0)) return fail(nullptr, BCCB_ERR_INVALID_ARG, "ADMM needs rho > 0");
+
+  bccb_solver* s = new bccb_solver;
+  s->n = n;
+  s->algo = algo;
+  s->rho = (algo == BCCB_ADMM) ? rho : 1.0;
+  s->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  cudaGetDevice(&s->device);
+
+  std::vector<int> mask_idx;
+  std::vector<FusedInst> fused(n);
+  std::map<std::pair<int, int>, std::vector<int>> by_shape;
+  int64_t mm_off = 0, g_off = 0;
+  for (int i = 0; i < n; ++i) {
+    const bccb_inst_t& q = insts[i];
+    if (q.M1 < 1 || q.M2 < 1 || q.mask_off < 0 || q.y_off < 0 || q.c_off < 0 || q.reserved != 0) {
+      delete s;
+      return fail(nullptr, BCCB_ERR_INVALID_ARG, "instance " + std::to_string(i) + ": bad M1/M2/offsets");
+    }
+    if (!is_pow2(q.L1) || !is_pow2(q.L2) || q.L1 < 16 || q.L2 < 16 || q.L1 > 256 || q.L2 > 256) {
+      delete s;
+      return fail(nullptr, BCCB_ERR_UNSUPPORTED,
+                  "instance " + std::to_string(i) + ": L1, L2 must be powers of two in [16, 256]");
+    }
+    if (!(q.lam >= 0.0)) {
+      delete s;
+      return fail(nullptr, BCCB_ERR_INVALID_ARG, "instance " + std::to_string(i) + ": lam must be >= 0");
+    }
+    const bccb::FusedEntry* fe = bccb::fused_lookup(q.L1, q.L2, algo == BCCB_ADMM);
+    if (!fe) {
+      delete s;
+      return fail(nullptr, BCCB_ERR_UNSUPPORTED, "no fused kernel for this grid");
+    }
+    InstDesc d;
+    d.M1 = q.M1;
+    d.M2 = q.M2;
+    d.L1 = q.L1;
+    d.L2 = q.L2;
+    d.lam_is_frac = q.lam_is_frac ? 1 : 0;
+    d.mask_off = mm_off;
+    d.y_off = q.y_off;
+    d.c_off = q.c_off;
+    d.g_off = g_off;
+    d.lam = q.lam;
+    int cnt = 0;
+    const uint8_t* m = masks_host + q.mask_off;
+    for (int pos = 0; pos < q.M1 * q.M2; ++pos) mask_idx.push_back(m[pos] ? cnt++ : -1);
+    if (cnt == 0) {
+      delete s;
+      return fail(nullptr, BCCB_ERR_INVALID_ARG, "instance " + std::to_string(i) + ": empty mask");
+    }
+    d.N = cnt;
+    s->h_desc.push_back(d);
+    fused[i].g_off = g_off;
+    fused[i].c_off = q.c_off;
+    fused[i].kappa = 0.f;
+    fused[i].pad_ = 0;
+    by_shape[{q.L1, q.L2}].push_back(i);
+    mm_off += (int64_t)q.M1 * q.M2;
+    g_off += (int64_t)q.L1 * q.L2;
+    s->total_y = std::max<int64_t>(s->total_y, q.y_off + cnt);
+    s->total_c = std::max<int64_t>(s->total_c, q.c_off + (int64_t)q.L1 * q.L2);
+    s->max_L1 = std::max(s->max_L1, q.L1);
+    s->max_L2 = std::max(s->max_L2, q.L2);
+  }
+  s->total_L = g_off;
+  s->total_MM = mm_off;
+
+  // class-sorted instance ids; largest grids first so they start earliest
+  std::vector<std::pair<int, std::pair<int, int>>> order;
+  for (auto& kv : by_shape) order.push_back({-(kv.first.first * kv.first.second), kv.first});
+  std::sort(order.begin(), order.end());
+  std::vector<int> ids;
+  for (auto& o : order) {
+    auto& v = by_shape[o.second];
+    bccb::ShapeClass sc;
+    sc.entry = *bccb::fused_lookup(o.second.first, o.second.second, algo == BCCB_ADMM);
+    sc.first = (int)ids.size();
+    sc.count = (int)v.size();
+    ids.insert(ids.end(), v.begin(), v.end());
+    s->classes.push_back(sc);
+  }
+
+#define CREATE_CUDA(expr)                                                                               \
+  do {                                                                                                  \
+    cudaError_t e_ = (expr);                                                                            \
+    if (e_ != cudaSuccess) {                                                                            \
+      std::string msg = std::string(#expr) + ": " + cudaGetErrorString(e_);                             \
+      release(s);                                                                                       \
+      delete s;                                                                                         \
+      return fail(nullptr, BCCB_ERR_CUDA, msg);                                                         \
+    }                                                                                                   \
+  } while (0)
+
+  CREATE_CUDA(dalloc(&s->d_desc, n));
+  CREATE_CUDA(dalloc(&s->d_mask_idx, mask_idx.size()));
+  CREATE_CUDA(dalloc(&s->d_lam64, s->total_L));
+  CREATE_CUDA(dalloc(&s->d_b64, s->total_L));
+  CREATE_CUDA(dalloc(&s->d_w64, s->total_L));
+  CREATE_CUDA(dalloc(&s->d_mult, s->total_L));
+  CREATE_CUDA(dalloc(&s->d_cterm, s->total_L));
+  CREATE_CUDA(dalloc(&s->d_par, n));
+  CREATE_CUDA(dalloc(&s->d_fused, n));
+  CREATE_CUDA(dalloc(&s->d_ids, n));
+  CREATE_CUDA(dalloc(&s->d_kkt, n));
+  CREATE_CUDA(dalloc(&s->d_obj, n));
+  CREATE_CUDA(dalloc(&s->d_red, n));
+  CREATE_CUDA(dalloc(&s->d_tw32, bccb::kTwiddleLen));
+  CREATE_CUDA(dalloc(&s->d_tw64, bccb::kTwiddleLen));
+  CREATE_CUDA(cudaMemcpy(s->d_desc, s->h_desc.data(), n * sizeof(InstDesc), cudaMemcpyHostToDevice));
+  CREATE_CUDA(cudaMemcpy(s->d_mask_idx, mask_idx.data(), mask_idx.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CREATE_CUDA(cudaMemcpy(s->d_fused, fused.data(), n * sizeof(FusedInst), cudaMemcpyHostToDevice));
+  CREATE_CUDA(cudaMemcpy(s->d_ids, ids.data(), n * sizeof(int), cudaMemcpyHostToDevice));
+  CREATE_CUDA(bccb::fill_twiddles(s));
+  for (auto& c : s->classes) CREATE_CUDA(c.entry.prepare());
+#undef CREATE_CUDA
+  *out = s;
+  return BCCB_OK;
+}
+
+int bccb_batch_solve(bccb_solver_t s, const void* y_dev, int iters, const void* c0_dev, void* c_out_dev,
+                     void* aux_out_dev, int check) {
+  if (!s) return fail(nullptr, BCCB_ERR_INVALID_ARG, "solver is NULL");
+  s->last_error.clear();
+  if (!y_dev || !c_out_dev) return fail(s, BCCB_ERR_INVALID_ARG, "y and c_out must be device pointers");
+  if (iters < 1) return fail(s, BCCB_ERR_INVALID_ARG, "iters must be >= 1");
+  BCCB_CUDA(s, cudaSetDevice(s->device));
+  s->launches = 0;
+  if (s->timing) BCCB_CUDA(s, cudaEventRecord(s->ev[0], s->stream));
+  if (s->algo == BCCB_FISTA) BCCB_CUDA(s, bccb::fista_schedule(s, iters));
+  const float2* y = reinterpret_cast<const float2*>(y_dev);
+  BCCB_CUDA(s, bccb::run_setup(s, y));
+  if (s->timing) BCCB_CUDA(s, cudaEventRecord(s->ev[1], s->stream));
+  FusedArgs a;
+  a.insts = s->d_fused;
+  a.beta = (s->algo == BCCB_FISTA) ? s->d_beta : nullptr;
+  a.twiddle = s->d_tw32;
+  a.mult = s->d_mult;
+  a.cterm = s->d_cterm;
+  a.c0 = reinterpret_cast<const float2*>(c0_dev);
+  a.c_out = reinterpret_cast<float2*>(c_out_dev);
+  a.aux_out = (s->algo == BCCB_ADMM) ? reinterpret_cast<float2*>(aux_out_dev) : nullptr;
+  a.iters = iters;
+  a.pad_ = 0;
+  for (const auto& c : s->classes) {
+    a.ids = s->d_ids + c.first;
+    BCCB_CUDA(s, c.entry.launch(a, c.count, s->stream));
+    s->launches += 1;
+  }
+  if (s->timing) BCCB_CUDA(s, cudaEventRecord(s->ev[2], s->stream));
+  if (check) BCCB_CUDA(s, bccb::run_check(s, y, reinterpret_cast<const float2*>(c_out_dev)));
+  if (s->timing) BCCB_CUDA(s, cudaEventRecord(s->ev[3], s->stream));
+  s->last_checked = check != 0;
+  return BCCB_OK;
+}
+
+int bccb_batch_solve_host(bccb_solver_t s, const void* y_host, int iters, void* c_out_host, int check) {
+  if (!s) return fail(nullptr, BCCB_ERR_INVALID_ARG, "solver is NULL");
+  if (!y_host || !c_out_host) return fail(s, BCCB_ERR_INVALID_ARG, "y and c_out must be host pointers");
+  BCCB_CUDA(s, cudaSetDevice(s->device));
+  if (!s->d_y_stage) BCCB_CUDA(s, dalloc(&s->d_y_stage, s->total_y));
+  if (!s->d_c_stage) BCCB_CUDA(s, dalloc(&s->d_c_stage, s->total_c));
+  BCCB_CUDA(s, cudaMemcpyAsync(s->d_y_stage, y_host, s->total_y * sizeof(float2), cudaMemcpyHostToDevice,
+                               s->stream));
+  int st = bccb_batch_solve(s, s->d_y_stage, iters, nullptr, s->d_c_stage, nullptr, check);
+  if (st != BCCB_OK) return st;
+  BCCB_CUDA(s, cudaMemcpyAsync(c_out_host, s->d_c_stage, s->total_c * sizeof(float2), cudaMemcpyDeviceToHost,
+                               s->stream));
+  BCCB_CUDA(s, cudaStreamSynchronize(s->stream));
+  return BCCB_OK;
+}
+
+int bccb_batch_results(bccb_solver_t s, double* kkt, double* obj, double* lam, double* mu) {
+  if (!s) return fail(nullptr, BCCB_ERR_INVALID_ARG, "solver is NULL");
+  BCCB_CUDA(s, cudaSetDevice(s->device));
+  BCCB_CUDA(s, cudaStreamSynchronize(s->stream));
+  if (kkt) BCCB_CUDA(s, cudaMemcpy(kkt, s->d_kkt, s->n * sizeof(double), cudaMemcpyDeviceToHost));
+  if (obj) BCCB_CUDA(s, cudaMemcpy(obj, s->d_obj, s->n * sizeof(double), cudaMemcpyDeviceToHost));
+  if (lam || mu) {
+    std::vector<InstParams> p(s->n);
+    BCCB_CUDA(s, cudaMemcpy(p.data(), s->d_par, s->n * sizeof(InstParams), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < s->n; ++i) {
+      if (lam) lam[i] = p[i].lam;
+      if (mu) mu[i] = p[i].mu;
+    }
+  }
+  return BCCB_OK;
+}
+
+int bccb_batch_get(bccb_solver_t s, int what, void* dst_dev) {
+  if (!s) return fail(nullptr, BCCB_ERR_INVALID_ARG, "solver is NULL");
+  if (!dst_dev || what < 0 || what > 3) return fail(s, BCCB_ERR_INVALID_ARG, "bad what / dst");
+  BCCB_CUDA(s, cudaSetDevice(s->device));
+  const void* src = what == 0 ? (const void*)s->d_lam64
+                  : what == 1 ? (const void*)s->d_b64
+                  : what == 2 ? (const void*)s->d_mult
+                              : (const void*)s->d_cterm;
+  const size_t es = what == 0 ? 8 : what == 1 ? 16 : what == 2 ? 4 : 8;
+  for (const InstDesc& d : s->h_desc) {
+    BCCB_CUDA(s, cudaMemcpyAsync((char*)dst_dev + d.c_off * es, (const char*)src + d.g_off * es,
+                                 (size_t)d.L1 * d.L2 * es, cudaMemcpyDeviceToDevice, s->stream));
+  }
+  return BCCB_OK;
+}
+
+int bccb_create(bccb_solver_t* out, int M1, int M2, const uint8_t* mask_host, int L1, int L2, int algo, double rho,
+                void* cuda_stream) {
+  bccb_inst_t q;
+  memset(&q, 0, sizeof(q));
+  q.M1 = M1;
+  q.M2 = M2;
+  q.L1 = L1;
+  q.L2 = L2;
+  q.lam = 0.0;
+  return bccb_batch_create(out, &q, 1, mask_host, algo, rho, cuda_stream);
+}
+
+int bccb_solve(bccb_solver_t s, const void* y_dev, double lam, int lam_is_frac, int iters, const void* c0_dev,
+               void* c_out_dev, void* aux_out_dev, double* kkt_out, double* obj_out) {
+  if (!s) return fail(nullptr, BCCB_ERR_INVALID_ARG, "solver is NULL");
+  if (s->n != 1) return fail(s, BCCB_ERR_INVALID_ARG, "bccb_solve needs a single-instance solver");
+  if (!(lam >= 0.0)) return fail(s, BCCB_ERR_INVALID_ARG, "lam must be >= 0");
+  BCCB_CUDA(s, cudaSetDevice(s->device));
+  if (s->h_desc[0].lam != lam || s->h_desc[0].lam_is_frac != (lam_is_frac ? 1 : 0)) {
+    s->h_desc[0].lam = lam;
+    s->h_desc[0].lam_is_frac = lam_is_frac ? 1 : 0;
+    BCCB_CUDA(s, cudaMemcpyAsync(s->d_desc, s->h_desc.data(), sizeof(InstDesc), cudaMemcpyHostToDevice, s->stream));
+    BCCB_CUDA(s, cudaStreamSynchronize(s->stream));
+  }
+  const int check = (kkt_out || obj_out) ? 1 : 0;
+  int st = bccb_batch_solve(s, y_dev, iters, c0_dev, c_out_dev, aux_out_dev, check);
+  if (st != BCCB_OK) return st;
+  if (check) return bccb_batch_results(s, kkt_out, obj_out, nullptr, nullptr);
+  return BCCB_OK;
+}
+
+int bccb_set_timing(bccb_solver_t s, int enable) {
+  if (!s) return fail(nullptr, BCCB_ERR_INVALID_ARG, "solver is NULL");
+  BCCB_CUDA(s, cudaSetDevice(s->device));
+  if (enable && !s->ev[0])
+    for (int i = 0; i < 4; ++i) BCCB_CUDA(s, cudaEventCreate(&s->ev[i]));
+  s->timing = enable != 0;
+  return BCCB_OK;
+}
+
+int bccb_last_timing(bccb_solver_t s, float* setup_ms, float* iterate_ms, float* check_ms, int64_t* launches) {
+  if (!s) return fail(nullptr, BCCB_ERR_INVALID_ARG, "solver is NULL");
+  float t[3] = {0.f, 0.f, 0.f};
+  if (s->timing) {
+    BCCB_CUDA(s, cudaSetDevice(s->device));
+    BCCB_CUDA(s, cudaEventSynchronize(s->ev[3]));
+    for (int i = 0; i < 3; ++i) BCCB_CUDA(s, cudaEventElapsedTime(&t[i], s->ev[i], s->ev[i + 1]));
+  }
+  if (setup_ms) *setup_ms = t[0];
+  if (iterate_ms) *iterate_ms = t[1];
+  if (check_ms) *check_ms = s->last_checked ? t[2] : 0.f;
+  if (launches) *launches = s->launches;
+  return BCCB_OK;
+}
+
+int bccb_batch_size(bccb_solver_t s, int* n) {
+  if (!s || !n) return fail(s, BCCB_ERR_INVALID_ARG, "NULL argument");
+  *n = s->n;
+  return BCCB_OK;
+}
+
+int bccb_instance_shape(bccb_solver_t s, int i, int* L1, int* L2, int* N) {
+  if (!s || i < 0 || i >= s->n) return fail(s, BCCB_ERR_INVALID_ARG, "bad solver or index");
+  if (L1) *L1 = s->h_desc[i].L1;
+  if (L2) *L2 = s->h_desc[i].L2;
+  if (N) *N = s->h_desc[i].N;
+  return BCCB_OK;
+}
+
+int bccb_destroy(bccb_solver_t s) {
+  if (!s) return BCCB_OK;
+  cudaSetDevice(s->device);
+  cudaStreamSynchronize(s->stream);
+  for (int i = 0; i < 4; ++i)
+    if (s->ev[i]) cudaEventDestroy(s->ev[i]);
+  release(s);
+  delete s;
+  return BCCB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,392 @@
+// One-time FP64 work around the FP32 iterations:
+//   * Lambda: the eigenvalues of the BCCB Gram A^H A, computed as the 2D DFT of its
+//     first column (eq:lambda, property (iv)).  The first column itself,
+//     g(k) = sum_n exp(+j 2 pi (k1 m1_n/L1 + k2 m2_n/L2)), is the unnormalised inverse
+//     2D DFT of the element-count grid (kept elements folded modulo (L1, L2)).
+//   * mu = 1 / sigma_max(A)^2 = 1 / max Lambda (eq:ista).
+//   * b = A^H y: with gamma = 1/2 the dictionary entry is (-1)^(m1+m2) times a DFT
+//     kernel, so b is the unnormalised inverse 2D DFT of the grid holding
+//     (-1)^(m1+m2) y_n at (m1 mod L1, m2 mod L2) (eq:ista, eq:admm).
+//   * ADMM's precomputed term d = (A^H A + rho I)^{-1} b, applied in the Fourier domain
+//     as IFFT2(FFT2(b)/(Lambda + rho)) (eq:admm, Section III-B).
+//   * the final check: r = A^H (y - A c) = b - G c, the relative KKT residual of the
+//     1/2-scaled LASSO, and the objective 1/2 ||y - A c||^2 + lam ||c||_1.
+// The FP64 2D DFTs are plain radix-2 Stockham passes (rows, then columns) over
+// global memory with each row / column tile staged in shared memory.
+#include <math.h>
+
+#include <vector>
+
+#include "solver.h"
+
+namespace bccb {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ double2* stockham64(double2* x, double2* y, int n, int cnt, int inv, const double2* tw) {
+  const int half = n >> 1;
+  for (int Ns = 1; Ns < n; Ns <<= 1) {
+    for (int idx = threadIdx.x; idx < half * cnt; idx += blockDim.x) {
+      const int q = idx % cnt, j = idx / cnt;
+      double2 a = x[j * cnt + q], b = x[(j + half) * cnt + q];
+      const int kk = j & (Ns - 1);
+      const double2 w = tw[kk * (kTwiddleLen / (2 * Ns))];
+      b = inv ? cmulc(b, w) : cmul(b, w);
+      const int o = ((j - kk) << 1) + kk;
+      y[o * cnt + q] = cadd(a, b);
+      y[(o + Ns) * cnt + q] = csub(a, b);
+    }
+    __syncthreads();
+    double2* t = x;
+    x = y;
+    y = t;
+  }
+  return x;
+}
+
+// In-place DFT of every row (length L1) of every instance's grid.
+__global__ void fft64_rows_kernel(const InstDesc* __restrict__ desc, double2* base, int inv,
+                                  const double2* __restrict__ tw) {
+  const InstDesc d = desc[blockIdx.x];
+  if ((int)blockIdx.y >= d.L2) return;
+  extern __shared__ double2 sm64[];
+  double2* x = sm64;
+  double2* y = sm64 + d.L1;
+  double2* g = base + d.g_off + (int64_t)blockIdx.y * d.L1;
+  for (int e = threadIdx.x; e < d.L1; e += blockDim.x) x[e] = g[e];
+  __syncthreads();
+  const double2* out = stockham64(x, y, d.L1, 1, inv, tw);
+  for (int e = threadIdx.x; e < d.L1; e += blockDim.x) g[e] = out[e];
+}
+
+constexpr int kColsPerBlock = 8;
+
+// In-place DFT of every column (length L2) of every instance's grid, kColsPerBlock at a time.
+__global__ void fft64_cols_kernel(const InstDesc* __restrict__ desc, double2* base, int inv,
+                                  const double2* __restrict__ tw) {
+  const InstDesc d = desc[blockIdx.x];
+  const int c0 = blockIdx.y * kColsPerBlock;
+  if (c0 >= d.L1) return;
+  const int cnt = min(kColsPerBlock, d.L1 - c0);
+  extern __shared__ double2 sm64[];
+  double2* x = sm64;
+  double2* y = sm64 + d.L2 * cnt;
+  double2* g = base + d.g_off;
+  for (int idx = threadIdx.x; idx < d.L2 * cnt; idx += blockDim.x) {
+    const int e = idx / cnt, q = idx % cnt;
+    x[idx] = g[(int64_t)e * d.L1 + c0 + q];
+  }
+  __syncthreads();
+  const double2* out = stockham64(x, y, d.L2, cnt, inv, tw);
+  for (int idx = threadIdx.x; idx < d.L2 * cnt; idx += blockDim.x) {
+    const int e = idx / cnt, q = idx % cnt;
+    g[(int64_t)e * d.L1 + c0 + q] = out[idx];
+  }
+}
+
+// count grid (for Lambda) and the signed measurement grid (for b)
+__global__ void scatter_kernel(const InstDesc* __restrict__ desc, const int* __restrict__ mask_idx,
+                               const float2* __restrict__ y, double2* cnt_grid, double2* meas_grid) {
+  const InstDesc d = desc[blockIdx.x];
+  const int L = d.L1 * d.L2;
+  const int* mi = mask_idx + d.mask_off;
+  const float2* yi = y + d.y_off;
+  for (int cell = blockIdx.y * blockDim.x + threadIdx.x; cell < L; cell += gridDim.y * blockDim.x) {
+    const int p1 = cell % d.L1, p2 = cell / d.L1;
+    double cnt = 0.0;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int m2 = p2; m2 < d.M2; m2 += d.L2) {
+      for (int m1 = p1; m1 < d.M1; m1 += d.L1) {
+        const int n = mi[m1 + m2 * d.M1];
+        if (n >= 0) {
+          cnt += 1.0;
+          const double sgn = ((m1 + m2) & 1) ? -1.0 : 1.0;
+          acc.x += sgn * (double)yi[n].x;
+          acc.y += sgn * (double)yi[n].y;
+        }
+      }
+    }
+    cnt_grid[d.g_off + cell] = make_double2(cnt, 0.0);
+    meas_grid[d.g_off + cell] = acc;
+  }
+}
+
+template <typename T, typename Op>
+__device__ T block_reduce(T v, Op op, T* sh, T identity) {
+  for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = (l < (int)(blockDim.x >> 5)) ? sh[l] : identity;
+    for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (l == 0) sh[0] = v;
+  }
+  __syncthreads();
+  v = sh[0];
+  __syncthreads();
+  return v;
+}
+
+struct MaxOp {
+  __device__ double operator()(double a, double b) const { return fmax(a, b); }
+};
+struct SumOp {
+  __device__ double operator()(double a, double b) const { return a + b; }
+};
+
+// Lambda, mu, lam, kappa, the FP32 multiplier and (ISTA/FISTA) the constant term mu*b.
+__global__ void eig_params_kernel(const InstDesc* __restrict__ desc, const double2* __restrict__ lam_c,
+                                  const double2* __restrict__ b64, double* lam64, InstParams* par,
+                                  float* mult, float2* cterm, FusedInst* fused, int algo, double rho) {
+  __shared__ double sh[32];
+  const InstDesc d = desc[blockIdx.x];
+  const int L = d.L1 * d.L2;
+  double top = 0.0, bmax = 0.0;
+  for (int cell = threadIdx.x; cell < L; cell += blockDim.x) {
+    const double lv = lam_c[d.g_off + cell].x;
+    lam64[d.g_off + cell] = lv;
+    top = fmax(top, lv);
+    const double2 bv = b64[d.g_off + cell];
+    bmax = fmax(bmax, sqrt(bv.x * bv.x + bv.y * bv.y));
+  }
+  top = block_reduce(top, MaxOp(), sh, 0.0);
+  bmax = block_reduce(bmax, MaxOp(), sh, 0.0);
+  const double mu = 1.0 / top;
+  const double lam = d.lam_is_frac ? d.lam * bmax : d.lam;
+  const double inv_L = 1.0 / (double)L;
+  for (int cell = threadIdx.x; cell < L; cell += blockDim.x) {
+    const double lv = lam64[d.g_off + cell];
+    double m;
+    if (algo == 2) {
+      m = rho / (lv + rho) * inv_L;
+    } else {
+      m = (1.0 - mu * lv) * inv_L;
+      const double2 bv = b64[d.g_off + cell];
+      cterm[d.g_off + cell] = make_float2((float)(mu * bv.x), (float)(mu * bv.y));
+    }
+    mult[d.g_off + cell] = (float)m;
+  }
+  if (threadIdx.x == 0) {
+    InstParams p;
+    p.mu = mu;
+    p.lam = lam;
+    p.lmax = bmax;
+    p.lam_top = top;
+    par[blockIdx.x] = p;
+    fused[blockIdx.x].kappa = (float)(algo == 2 ? lam / rho : mu * lam);
+  }
+}
+
+__global__ void copy_grid_kernel(const InstDesc* __restrict__ desc, const double2* __restrict__ src,
+                                 double2* dst) {
+  const InstDesc d = desc[blockIdx.x];
+  const int L = d.L1 * d.L2;
+  for (int cell = blockIdx.y * blockDim.x + threadIdx.x; cell < L; cell += gridDim.y * blockDim.x)
+    dst[d.g_off + cell] = src[d.g_off + cell];
+}
+
+// w <- w / (Lambda + rho)
+__global__ void admm_divide_kernel(const InstDesc* __restrict__ desc, const double* __restrict__ lam64,
+                                   double2* w, double rho) {
+  const InstDesc d = desc[blockIdx.x];
+  const int L = d.L1 * d.L2;
+  for (int cell = blockIdx.y * blockDim.x + threadIdx.x; cell < L; cell += gridDim.y * blockDim.x) {
+    const double s = 1.0 / (lam64[d.g_off + cell] + rho);
+    const double2 v = w[d.g_off + cell];
+    w[d.g_off + cell] = make_double2(v.x * s, v.y * s);
+  }
+}
+
+// cterm <- w / (L1 L2)  (normalises the inverse DFT)
+__global__ void cterm_from_w_kernel(const InstDesc* __restrict__ desc, const double2* __restrict__ w,
+                                    float2* cterm) {
+  const InstDesc d = desc[blockIdx.x];
+  const int L = d.L1 * d.L2;
+  const double s = 1.0 / (double)L;
+  for (int cell = blockIdx.y * blockDim.x + threadIdx.x; cell < L; cell += gridDim.y * blockDim.x) {
+    const double2 v = w[d.g_off + cell];
+    cterm[d.g_off + cell] = make_float2((float)(v.x * s), (float)(v.y * s));
+  }
+}
+
+// w <- c (FP32 solution, solver grid layout)
+__global__ void load_solution_kernel(const InstDesc* __restrict__ desc, const float2* __restrict__ c,
+                                     double2* w) {
+  const InstDesc d = desc[blockIdx.x];
+  const int L = d.L1 * d.L2;
+  for (int cell = blockIdx.y * blockDim.x + threadIdx.x; cell < L; cell += gridDim.y * blockDim.x) {
+    const float2 v = c[d.c_off + cell];
+    w[d.g_off + cell] = make_double2((double)v.x, (double)v.y);
+  }
+}
+
+// sum_n |y_n - (A c)_n|^2 with (A c)_n = (-1)^(m1+m2) FFT2(c)[m2 mod L2, m1 mod L1]
+__global__ void data_residual_kernel(const InstDesc* __restrict__ desc, const int* __restrict__ mask_idx,
+                                     const float2* __restrict__ y, const double2* __restrict__ cf,
+                                     double* red) {
+  __shared__ double sh[32];
+  const InstDesc d = desc[blockIdx.x];
+  const int* mi = mask_idx + d.mask_off;
+  const float2* yi = y + d.y_off;
+  double acc = 0.0;
+  for (int pos = threadIdx.x; pos < d.M1 * d.M2; pos += blockDim.x) {
+    const int n = mi[pos];
+    if (n < 0) continue;
+    const int m1 = pos % d.M1, m2 = pos / d.M1;
+    const double sgn = ((m1 + m2) & 1) ? -1.0 : 1.0;
+    const double2 v = cf[d.g_off + (int64_t)(m2 % d.L2) * d.L1 + (m1 % d.L1)];
+    const double ex = (double)yi[n].x - sgn * v.x, ey = (double)yi[n].y - sgn * v.y;
+    acc += ex * ex + ey * ey;
+  }
+  acc = block_reduce(acc, SumOp(), sh, 0.0);
+  if (threadIdx.x == 0) red[blockIdx.x] = acc;
+}
+
+__global__ void mul_lambda_kernel(const InstDesc* __restrict__ desc, const double* __restrict__ lam64,
+                                  double2* w) {
+  const InstDesc d = desc[blockIdx.x];
+  const int L = d.L1 * d.L2;
+  for (int cell = blockIdx.y * blockDim.x + threadIdx.x; cell < L; cell += gridDim.y * blockDim.x) {
+    const double s = lam64[d.g_off + cell];
+    const double2 v = w[d.g_off + cell];
+    w[d.g_off + cell] = make_double2(v.x * s, v.y * s);
+  }
+}
+
+// r = b - G c (G c = IFFT2(Lambda FFT2(c)), held unnormalised in w); KKT residual and objective
+__global__ void kkt_final_kernel(const InstDesc* __restrict__ desc, const double2* __restrict__ b64,
+                                 const double2* __restrict__ gc, const float2* __restrict__ c,
+                                 const InstParams* __restrict__ par, const double* __restrict__ red,
+                                 double* kkt, double* obj) {
+  __shared__ double sh[32];
+  const InstDesc d = desc[blockIdx.x];
+  const int L = d.L1 * d.L2;
+  const double lam = par[blockIdx.x].lam;
+  const double inv_L = 1.0 / (double)L;
+  double worst = 0.0, l1 = 0.0;
+  for (int cell = threadIdx.x; cell < L; cell += blockDim.x) {
+    const double2 bv = b64[d.g_off + cell];
+    const double2 gv = gc[d.g_off + cell];
+    const double rx = bv.x - gv.x * inv_L, ry = bv.y - gv.y * inv_L;
+    const float2 cv = c[d.c_off + cell];
+    const double cx = cv.x, cy = cv.y;
+    const double mag = sqrt(cx * cx + cy * cy);
+    double viol;
+    if (mag > 0.0) {
+      const double ex = rx - lam * cx / mag, ey = ry - lam * cy / mag;
+      viol = sqrt(ex * ex + ey * ey);
+    } else {
+      viol = fmax(sqrt(rx * rx + ry * ry) - lam, 0.0);
+    }
+    worst = fmax(worst, viol);
+    l1 += mag;
+  }
+  worst = block_reduce(worst, MaxOp(), sh, 0.0);
+  l1 = block_reduce(l1, SumOp(), sh, 0.0);
+  if (threadIdx.x == 0) {
+    kkt[blockIdx.x] = lam > 0.0 ? worst / lam : worst;
+    obj[blockIdx.x] = 0.5 * red[blockIdx.x] + lam * l1;
+  }
+}
+
+__global__ void fista_beta_kernel(float* beta, int iters) {
+  // alpha_1 = 1, alpha_(t+1) = (1 + sqrt(1 + 4 alpha_t^2))/2, beta_t = (alpha_t - 1)/alpha_(t+1),
+  // evaluated in FP64 with explicit round-to-nearest operations (no contraction).
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double a = 1.0;
+  for (int t = 0; t < iters; ++t) {
+    const double an = __dmul_rn(__dadd_rn(1.0, __dsqrt_rn(__dadd_rn(1.0, __dmul_rn(__dmul_rn(4.0, a), a)))), 0.5);
+    beta[t] = (float)__ddiv_rn(__dadd_rn(a, -1.0), an);
+    a = an;
+  }
+}
+
+dim3 grid_cells(const bccb_solver* s) {
+  const int cells = s->max_L1 * s->max_L2;
+  const int blocks = (cells + kThreads - 1) / kThreads;
+  return dim3((unsigned)s->n, (unsigned)(blocks < 64 ? blocks : 64));
+}
+
+cudaError_t fft2_64(bccb_solver* s, double2* grid, int inv) {
+  s->launches += 2;
+  const size_t smr = (size_t)2 * s->max_L1 * sizeof(double2);
+  fft64_rows_kernel<<<dim3(s->n, s->max_L2), 128, smr, s->stream>>>(s->d_desc, grid, inv, s->d_tw64);
+  const size_t smc = (size_t)2 * s->max_L2 * kColsPerBlock * sizeof(double2);
+  fft64_cols_kernel<<<dim3(s->n, (s->max_L1 + kColsPerBlock - 1) / kColsPerBlock), 128, smc, s->stream>>>(
+      s->d_desc, grid, inv, s->d_tw64);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t fill_twiddles(bccb_solver* s) {
+  // the column pass stages kColsPerBlock columns of length L2 twice (ping-pong)
+  const int col_smem = 2 * s->max_L2 * kColsPerBlock * (int)sizeof(double2);
+  cudaError_t e0 = cudaFuncSetAttribute(fft64_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem);
+  if (e0 != cudaSuccess) return e0;
+  std::vector<float2> t32(kTwiddleLen);
+  std::vector<double2> t64(kTwiddleLen);
+  for (int e = 0; e < kTwiddleLen; ++e) {
+    const double ang = -2.0 * M_PI * (double)e / (double)kTwiddleLen;
+    t64[e] = make_double2(cos(ang), sin(ang));
+    t32[e] = make_float2((float)cos(ang), (float)sin(ang));
+  }
+  cudaError_t err = cudaMemcpy(s->d_tw32, t32.data(), kTwiddleLen * sizeof(float2), cudaMemcpyHostToDevice);
+  if (err != cudaSuccess) return err;
+  return cudaMemcpy(s->d_tw64, t64.data(), kTwiddleLen * sizeof(double2), cudaMemcpyHostToDevice);
+}
+
+cudaError_t fista_schedule(bccb_solver* s, int iters) {
+  if (iters <= 0 || s->beta_len == iters) return cudaSuccess;
+  if (iters > s->beta_cap) {
+    if (s->d_beta) cudaFree(s->d_beta);
+    s->d_beta = nullptr;
+    cudaError_t err = cudaMalloc(&s->d_beta, (size_t)iters * sizeof(float));
+    if (err != cudaSuccess) return err;
+    s->beta_cap = iters;
+  }
+  fista_beta_kernel<<<1, 32, 0, s->stream>>>(s->d_beta, iters);
+  s->launches += 1;
+  s->beta_len = iters;
+  return cudaGetLastError();
+}
+
+cudaError_t run_setup(bccb_solver* s, const float2* y_dev) {
+  const dim3 gc = grid_cells(s);
+  scatter_kernel<<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_mask_idx, y_dev, s->d_w64, s->d_b64);
+  s->launches += 2 + (s->algo == 2 ? 3 : 0);  // scatter, eig_params (+ copy, divide, cterm)
+  cudaError_t err;
+  if ((err = fft2_64(s, s->d_w64, 1)) != cudaSuccess) return err;  // first column of the Gram
+  if ((err = fft2_64(s, s->d_b64, 1)) != cudaSuccess) return err;  // b = A^H y
+  if ((err = fft2_64(s, s->d_w64, 0)) != cudaSuccess) return err;  // Lambda (eq:lambda)
+  eig_params_kernel<<<s->n, kThreads, 0, s->stream>>>(s->d_desc, s->d_w64, s->d_b64, s->d_lam64, s->d_par,
+                                                       s->d_mult, s->d_cterm, s->d_fused, s->algo, s->rho);
+  if (s->algo == 2) {
+    copy_grid_kernel<<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_b64, s->d_w64);
+    if ((err = fft2_64(s, s->d_w64, 0)) != cudaSuccess) return err;
+    admm_divide_kernel<<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_lam64, s->d_w64, s->rho);
+    if ((err = fft2_64(s, s->d_w64, 1)) != cudaSuccess) return err;
+    cterm_from_w_kernel<<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_w64, s->d_cterm);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t run_check(bccb_solver* s, const float2* y_dev, const float2* c_dev) {
+  const dim3 gc = grid_cells(s);
+  load_solution_kernel<<<gc, kThreads, 0, s->stream>>>(s->d_desc, c_dev, s->d_w64);
+  s->launches += 4;  // load_solution, data_residual, mul_lambda, kkt_final
+  cudaError_t err;
+  if ((err = fft2_64(s, s->d_w64, 0)) != cudaSuccess) return err;
+  data_residual_kernel<<<s->n, kThreads, 0, s->stream>>>(s->d_desc, s->d_mask_idx, y_dev, s->d_w64, s->d_red);
+  mul_lambda_kernel<<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_lam64, s->d_w64);
+  if ((err = fft2_64(s, s->d_w64, 1)) != cudaSuccess) return err;
+  kkt_final_kernel<<<s->n, kThreads, 0, s->stream>>>(s->d_desc, s->d_b64, s->d_w64, c_dev, s->d_par, s->d_red,
+                                                      s->d_kkt, s->d_obj);
+  return cudaGetLastError();
+}
+
+}  // namespace bccb

@@ -1,0 +1,94 @@
+// Private solver state shared by the C-ABI implementation and the setup/check kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "fused_solve.cuh"
+
+namespace bccb {
+
+// One problem instance (device-visible).
+struct InstDesc {
+  int M1, M2, L1, L2, N;
+  int lam_is_frac;   // 1: lam is a fraction of ||A^H y||_inf
+  int64_t mask_off;  // into mask_idx (M1*M2 entries: y index or -1)
+  int64_t y_off;     // complex elements into the measurement buffer
+  int64_t c_off;     // complex elements into the solution buffer
+  int64_t g_off;     // elements into the per-grid arenas (L1*L2 each)
+  double lam;        // absolute lam, or fraction (see lam_is_frac)
+};
+
+// Per-instance scalars produced on the device by the setup kernels.
+struct InstParams {
+  double mu;      // 1 / max Lambda
+  double lam;     // absolute LASSO weight used
+  double lmax;    // ||A^H y||_inf
+  double lam_top; // max Lambda
+};
+
+struct ShapeClass {
+  FusedEntry entry;
+  int first;  // offset into the class-sorted id list
+  int count;
+};
+
+}  // namespace bccb
+
+struct bccb_solver {
+  int n = 0;
+  int algo = 1;
+  int prec = 0;
+  double rho = 1.0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int64_t total_L = 0;
+  int64_t total_MM = 0;
+  int64_t total_y = 0;
+  int64_t total_c = 0;
+  int max_L1 = 0, max_L2 = 0;
+  std::vector<bccb::InstDesc> h_desc;
+  std::vector<bccb::ShapeClass> classes;
+
+  bccb::InstDesc* d_desc = nullptr;
+  int* d_mask_idx = nullptr;
+  double* d_lam64 = nullptr;    // Lambda (real), per grid cell
+  double2* d_b64 = nullptr;     // b = A^H y (FP64)
+  double2* d_w64 = nullptr;     // FP64 FFT workspace
+  float* d_mult = nullptr;      // FP32 Fourier multiplier (includes 1/(L1 L2))
+  float2* d_cterm = nullptr;    // FP32 mu*b or d
+  bccb::InstParams* d_par = nullptr;
+  bccb::FusedInst* d_fused = nullptr;
+  int* d_ids = nullptr;
+  float* d_beta = nullptr;
+  int beta_cap = 0;
+  int beta_len = -1;
+  double* d_kkt = nullptr;
+  double* d_obj = nullptr;
+  double* d_red = nullptr;     // per-instance partial sums
+  float2* d_tw32 = nullptr;
+  double2* d_tw64 = nullptr;
+  // host staging for the host-buffer entry point
+  float2* d_y_stage = nullptr;
+  float2* d_c_stage = nullptr;
+  std::string last_error;
+  // profiling
+  bool timing = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  int64_t launches = 0;  // kernels launched by the last solve
+  bool last_checked = false;
+};
+
+namespace bccb {
+// setup_fp64.cu
+// each returns the CUDA status and adds its kernel launches to s->launches
+cudaError_t run_setup(bccb_solver* s, const float2* y_dev);
+cudaError_t run_check(bccb_solver* s, const float2* y_dev, const float2* c_dev);
+cudaError_t fill_twiddles(bccb_solver* s);
+cudaError_t fista_schedule(bccb_solver* s, int iters);
+// fused_L*.cu
+const FusedEntry* fused_lookup(int L1, int L2, bool admm);
+}  // namespace bccb

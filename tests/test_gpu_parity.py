@@ -1,0 +1,212 @@
+"""GPU parity: the CUDA path through the C-ABI against the FP64 oracle on the same
+seeded inputs (complex64 on the GPU, complex128 in the oracle)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import assert_parity, gpu_run, inst, oracle_run, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+def _snap(seed, M1, M2, N, L1, L2, K=3, snr=15.0, lam_frac=0.1, **kw):
+    s = synth.make_snapshot(seed, M1, M2, N, L1, L2, K, snr, **kw)
+    s.lam_frac = lam_frac
+    return s
+
+
+# ------------------------------------------------------------------------------------------
+# setup rows: Lambda (eq:lambda), b = A^H y, mu (eq:ista), lam = frac ||A^H y||_inf
+# ------------------------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("M1,M2,N,L1,L2", [(16, 16, 64, 64, 64), (8, 4, 12, 16, 32), (24, 6, 50, 16, 64),
+                                           (32, 32, 256, 256, 256), (20, 40, 300, 32, 32)])
+def test_setup_lambda_b_mu(lib, M1, M2, N, L1, L2):
+    import torch
+
+    s = _snap(100 + L1 + L2, M1, M2, N, L1, L2)
+    A = oracle.dictionary(s.mask, M1, M2, L1, L2)
+    lam_ref = oracle.gram_eigenvalues(A, L1, L2).real.reshape(-1)
+    b_ref = oracle.adjoint_measurements(A, s.y)
+    run = gpu_run(lib, [s], [0.1], "fista", 1)
+    solver = run["solver"]
+    lam_gpu = torch.zeros(L1 * L2, dtype=torch.float64, device="cuda")
+    b_gpu = torch.zeros(L1 * L2, dtype=torch.complex128, device="cuda")
+    solver.get(lib.GET_LAMBDA, lam_gpu)
+    solver.get(lib.GET_B, b_gpu)
+    torch.cuda.synchronize()
+    assert np.abs(lam_gpu.cpu().numpy() - lam_ref).max() <= 1e-9 * lam_ref.max()
+    # y enters the GPU as complex64, so b carries that rounding (about 6e-8 relative)
+    assert rel_err(b_gpu.cpu().numpy(), b_ref) <= 1e-6
+    assert abs(run["res"]["mu"][0] * oracle.step_size(A) ** -1 - 1.0) <= 1e-12
+
+
+def test_lambda_fraction_of_lmax(lib):
+    s = synth.config_snapshot(1, 3)
+    A = oracle.dictionary(s.mask, s.M1, s.M2, s.L1, s.L2)
+    run = gpu_run_frac(lib, s, 0.1)
+    assert abs(run["res"]["lam"][0] / (0.1 * oracle.lambda_max(A, s.y)) - 1.0) <= 1e-6
+
+
+def gpu_run_frac(lib, s, frac):
+    import torch
+
+    solver = lib.BatchSolver([inst(s, frac, lam_is_frac=True)], "fista")
+    y = torch.from_numpy(solver.y_host).cuda()
+    c = torch.zeros(solver.total_c, dtype=torch.complex64, device="cuda")
+    solver.solve(y, 5, c)
+    return dict(res=solver.results())
+
+
+# ------------------------------------------------------------------------------------------
+# full-size single-snapshot workloads
+# ------------------------------------------------------------------------------------------
+
+
+def test_fista_64x64_500_iterations(lib):
+    """Plain FISTA, 16x16 array, N=64, 64x64 grid, 3 on-grid sources, 20 dB, 500 iterations."""
+    s = synth.config_snapshot(1, 0)
+    ref = oracle_run(s, "fista", 500)
+    run = gpu_run(lib, [s], [ref["lam"]], "fista", 500)
+    assert_parity(run["c"][0], ref, what="fista 64x64")
+    assert run["res"]["kkt"][0] == pytest.approx(oracle.kkt_residual(ref["A"], s.y, run["c"][0].astype(np.complex128), ref["lam"]), abs=1e-4)
+
+
+@pytest.mark.parametrize("algo", ["ista", "fista", "admm"])
+def test_256x256_1000_iterations(lib, algo):
+    """32x32 array, N=256, 256x256 grid, 8 off-grid sources, 10 dB, 1000 iterations (ADMM rho=1)."""
+    s = synth.config_snapshot(2, 0)
+    ref = oracle_run(s, algo, 1000, rho=1.0)
+    run = gpu_run(lib, [s], [ref["lam"]], algo, 1000, rho=1.0)
+    assert_parity(run["c"][0], ref, what=f"{algo} 256x256")
+    if algo == "admm":
+        assert_parity(run["aux"][0], ref, ref_c=ref["aux"], what="admm c^(T)")
+
+
+# ------------------------------------------------------------------------------------------
+# every grid shape class (cluster sizes 1, 2, 4, 8) and non-square grids
+# ------------------------------------------------------------------------------------------
+
+SHAPES = [(16, 16), (32, 16), (16, 64), (64, 32), (128, 64), (256, 32), (32, 256), (128, 128), (256, 128),
+          (128, 256), (64, 256)]
+
+
+@pytest.mark.parametrize("algo", ["ista", "fista", "admm"])
+@pytest.mark.parametrize("L1,L2", SHAPES)
+def test_shapes(lib, algo, L1, L2):
+    M1, M2 = max(2, L1 // 4), max(2, L2 // 4)
+    s = _snap(7 * L1 + L2, M1, M2, max(1, (M1 * M2) // 4), L1, L2, K=4, snr=12.0, lam_frac=0.08)
+    iters = 150
+    ref = oracle_run(s, algo, iters, rho=4.0)
+    run = gpu_run(lib, [s], [ref["lam"]], algo, iters, rho=4.0)
+    assert_parity(run["c"][0], ref, what=f"{algo} {L1}x{L2}")
+
+
+# ------------------------------------------------------------------------------------------
+# batched, ragged shapes in one call
+# ------------------------------------------------------------------------------------------
+
+
+def test_ragged_batch_matches_oracle(lib):
+    snaps = synth.config_batch(3, 10)
+    refs = [oracle_run(s, "fista", 200) for s in snaps]
+    run = gpu_run(lib, snaps, [r["lam"] for r in refs], "fista", 200)
+    for i, (c, r) in enumerate(zip(run["c"], refs)):
+        assert_parity(c, r, what=f"batch instance {i} ({snaps[i].L1}x{snaps[i].L2})")
+        assert run["res"]["kkt"][i] == pytest.approx(
+            oracle.kkt_residual(r["A"], snaps[i].y, c.astype(np.complex128), r["lam"]), abs=1e-4)
+        assert run["res"]["objective"][i] == pytest.approx(
+            oracle.objective(r["A"], snaps[i].y, c.astype(np.complex128), r["lam"]), rel=1e-5)
+
+
+# ------------------------------------------------------------------------------------------
+# edge cases
+# ------------------------------------------------------------------------------------------
+
+
+def test_single_element_and_full_mask(lib):
+    s1 = _snap(41, 5, 4, 1, 16, 16, K=1, snr=None)
+    s2 = _snap(42, 6, 5, 30, 32, 16, K=2, snr=20.0)
+    for s in (s1, s2):
+        for algo in ("fista", "admm"):
+            ref = oracle_run(s, algo, 80, rho=2.0)
+            run = gpu_run(lib, [s], [ref["lam"]], algo, 80, rho=2.0)
+            assert_parity(run["c"][0], ref, what=f"{algo} N={s.N}")
+
+
+def test_folded_mask_wider_than_grid(lib):
+    """M1 > L1 and M2 > L2: the Gram is still BCCB with folded counts in Lambda."""
+    s = _snap(43, 24, 20, 60, 16, 16, K=2, snr=20.0)
+    for algo in ("ista", "fista", "admm"):
+        ref = oracle_run(s, algo, 120, rho=50.0)
+        run = gpu_run(lib, [s], [ref["lam"]], algo, 120, rho=50.0)
+        assert_parity(run["c"][0], ref, what=f"{algo} folded")
+
+
+def test_lambda_zero_and_above_lmax(lib):
+    s = _snap(44, 8, 8, 20, 32, 32, K=2, snr=10.0)
+    A = oracle.dictionary(s.mask, s.M1, s.M2, s.L1, s.L2)
+    lmax = oracle.lambda_max(A, s.y)
+    # lam = 0: one ISTA step gives A^H y / (L1 L2)
+    ref = oracle_run(s, "ista", 1, lam=0.0, A=A)
+    run = gpu_run(lib, [s], [0.0], "ista", 1)
+    assert rel_err(run["c"][0], ref["c"]) <= 1e-5
+    # lam above ||A^H y||_inf: the solution is exactly zero for every algorithm
+    for algo in ("ista", "fista", "admm"):
+        run = gpu_run(lib, [s], [1.01 * lmax], algo, 30)
+        assert np.count_nonzero(run["c"][0]) == 0
+
+
+def test_one_iteration_and_warm_start(lib):
+    s = _snap(45, 8, 8, 24, 64, 16, K=3, snr=15.0)
+    ref1 = oracle_run(s, "fista", 1)
+    run1 = gpu_run(lib, [s], [ref1["lam"]], "fista", 1)
+    assert_parity(run1["c"][0], ref1, what="fista 1 iteration")
+    # ISTA is memoryless: 40 iterations warm-started from 60 equal 100 from zero
+    ref = oracle_run(s, "ista", 100)
+    first = gpu_run(lib, [s], [ref["lam"]], "ista", 60)
+    second = gpu_run(lib, [s], [ref["lam"]], "ista", 40, c0=first["c"][0])
+    assert_parity(second["c"][0], ref, what="ista warm start")
+
+
+def test_host_entry_point_matches_device(lib):
+    snaps = synth.config_batch(3, 3, first=20)
+    lams = [0.1 * oracle.lambda_max(oracle.dictionary(s.mask, s.M1, s.M2, s.L1, s.L2), s.y) for s in snaps]
+    dev = gpu_run(lib, snaps, lams, "fista", 50)
+    solver = dev["solver"]
+    out = np.zeros(solver.total_c, np.complex64)
+    solver.solve_host(solver.y_host, 50, out)
+    np.testing.assert_array_equal(np.concatenate(dev["c"]), out)
+
+
+# ------------------------------------------------------------------------------------------
+# argument checks (no kernel runs for these)
+# ------------------------------------------------------------------------------------------
+
+
+def test_invalid_arguments(lib):
+    s = _snap(46, 4, 4, 6, 16, 16)
+    good = inst(s, 0.1)
+    for bad, status in [(dict(good, L1=48), lib.ERR_UNSUPPORTED), (dict(good, L2=512), lib.ERR_UNSUPPORTED),
+                        (dict(good, L1=8), lib.ERR_UNSUPPORTED),
+                        (dict(good, mask=np.zeros(16, np.uint8)), lib.ERR_INVALID_ARG),
+                        (dict(good, lam=-1.0), lib.ERR_INVALID_ARG)]:
+        with pytest.raises(lib.BccbError) as e:
+            lib.BatchSolver([bad], "fista")
+        assert e.value.status == status
+    with pytest.raises(lib.BccbError) as e:
+        lib.BatchSolver([good], "admm", rho=0.0)
+    assert e.value.status == lib.ERR_INVALID_ARG
+    with pytest.raises(lib.BccbError) as e:
+        lib.BatchSolver([good], 7)
+    assert e.value.status == lib.ERR_INVALID_ARG
+    import torch
+
+    solver = lib.BatchSolver([good], "fista")
+    y = torch.from_numpy(solver.y_host).cuda()
+    c = torch.zeros(solver.total_c, dtype=torch.complex64, device="cuda")
+    with pytest.raises(lib.BccbError) as e:
+        solver.solve(y, 0, c)
+    assert e.value.status == lib.ERR_INVALID_ARG
