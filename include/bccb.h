@@ -83,9 +83,10 @@ int bccb_batch_create(bccb_solver_t* out, const bccb_inst_t* insts, int n, const
 
 /* Run the whole hot path for every instance on the solver's stream:
  *   setup (FP64): Lambda = FFT2 of the Gram's first column (eq:lambda),
- *                 mu = 1/max Lambda (eq:ista), b = A^H y, lam, the FP32 Fourier
- *                 multiplier and the constant term mu*b (ISTA/FISTA) or
- *                 d = (G + rho I)^{-1} b (ADMM, "can be precomputed");
+ *                 mu = 1/max Lambda (eq:ista), b = A^H y, lam, and the FP32
+ *                 Fourier-domain multiplier q and constant term Bt: mu Lambda/L and
+ *                 mu FFT2(b)/L (ISTA/FISTA), Lambda/(Lambda+rho)/L and
+ *                 FFT2(b)/(Lambda+rho)/L (ADMM, the "precomputed" term of eq:admm);
  *   iterations (FP32): `iters` fused ISTA/FISTA/ADMM iterations, each one FFT2,
  *                 multiply, IFFT2 and the pointwise update (eq:ista/fista/admm, eq:Rc);
  *   check (FP64, if check != 0): relative KKT residual and objective per instance.
@@ -109,8 +110,9 @@ int bccb_batch_results(bccb_solver_t s, double* kkt, double* obj, double* lam, d
 
 /* Copy an internal per-instance grid of the last solve (device to device), packed
  * like c_out (instance i at its c_off).  what: 0 = Lambda (float64, real);
- * 1 = b = A^H y (complex128); 2 = the FP32 Fourier multiplier (float32, includes
- * 1/(L1 L2)); 3 = the FP32 constant term mu*b or d (complex64).  Asynchronous. */
+ * 1 = b = A^H y (complex128); 2 = the FP32 Fourier multiplier q (float32); 3 = the
+ * FP32 Fourier-domain constant term Bt (complex64); 2 and 3 are in frequency order
+ * [p2][p1] and include 1/(L1 L2).  Asynchronous. */
 int bccb_batch_get(bccb_solver_t s, int what, void* dst_dev);
 
 /* Single-instance convenience: a batch of one (c_off = y_off = 0). */

@@ -215,7 +215,7 @@ int bccb_batch_solve(bccb_solver_t s, const void* y_dev, int iters, const void* 
   a.beta = (s->algo == BCCB_FISTA) ? s->d_beta : nullptr;
   a.twiddle = s->d_tw32;
   a.mult = s->d_mult;
-  a.cterm = s->d_cterm;
+  a.bt = s->d_cterm;
   a.c0 = reinterpret_cast<const float2*>(c0_dev);
   a.c_out = reinterpret_cast<float2*>(c_out_dev);
   a.aux_out = (s->algo == BCCB_ADMM) ? reinterpret_cast<float2*>(aux_out_dev) : nullptr;

@@ -2,18 +2,24 @@
 // cluster (FP32, complex64 state).
 //
 // Each iteration applies the BCCB Gram operator through the 2D FFT (Section
-// III-B, eq:Rc):  x -> IFFT2(m . FFT2(x)), with the Fourier multiplier
-//   m = (1 - mu Lambda)/(L1 L2)      for ISTA/FISTA (eq:ista, eq:fista)
-//   m = rho/(Lambda + rho)/(L1 L2)   for ADMM       (eq:admm, c-update)
-// and fuses the rest of the iteration into the last inverse FFT stage:
-//   ISTA/FISTA: c <- S_kappa(u + mu b),  z <- c + beta_t (c - c_prev)
-//   ADMM:       c <- u + d, z <- S_kappa(c + v), v <- v + c - z, next input z - v.
+// III-B, eq:Rc).  The identity part of the iteration matrix never goes through
+// the FFT: with G' = IFFT2(q . FFT2(x) - Bt) (unnormalised inverse),
+//   ISTA/FISTA (eq:ista, eq:fista): q = mu Lambda/L, Bt = mu FFT2(b)/L, x = z^(t):
+//       u = z^(t) - G'  ( = (I - mu G) z^(t) + mu b ),  c^(t) = S_kappa(u),
+//       z^(t+1) = c^(t) + beta_t (c^(t) - c^(t-1));  ISTA has z^(t) = c^(t-1), beta = 0.
+//   ADMM (eq:admm):  q = Lambda/(Lambda + rho)/L, Bt = FFT2(b)/(Lambda + rho)/L, x = z - v:
+//       u = z^(t) - G'  ( = c^(t+1) + v^(t) ),  z^(t+1) = S_kappa(u),  v^(t+1) = u - z^(t+1).
+// The subtraction b - G x happens in the Fourier domain, where its operands are of
+// the size of the data residual, and directions the Gram does not see pass through
+// exactly; both keep FP32 round-off from being amplified by FISTA's momentum.
+// q and Bt vanish off the element mask (Lambda = 0), so the middle stage skips
+// those frequencies.
 //
 // Layout.  The grid is stored L2 rows x L1 columns, row-major (the paper's
 // vec(C) with C in C^{L1 x L2}, Section III-B).  A cluster of C CTAs owns one
 // instance; CTA c keeps global rows c + C*s (s = 0..R-1, R = L2/C) in shared
 // memory for the whole solve, so the iterations never touch HBM except for the
-// constant term (mu b or d), read through L2.
+// nonzero Fourier-domain multiplier entries, read through L2.
 //
 // Transform.  Row DFTs (length L1) are local.  The column DFT of length L2 is
 // split as L2 = Q * R' (decimation in time): group g = c + C*v (v < Q/C) holds
@@ -37,7 +43,7 @@ namespace cg = cooperative_groups;
 namespace bccb {
 
 struct FusedInst {
-  int64_t g_off;  // offset of this instance's grids in FusedArgs::mult / ::cterm
+  int64_t g_off;  // offset of this instance's grids in FusedArgs::mult / ::bt
   int64_t c_off;  // offset of this instance's solution in c_out / aux_out / c0
   float kappa;    // threshold mu*lam (ISTA/FISTA) or lam/rho (ADMM), set by the setup kernels
   int pad_;
@@ -48,8 +54,8 @@ struct FusedArgs {
   const int* ids;          // instance index for cluster k = blockIdx.x / C
   const float* beta;       // FISTA momentum beta_t (length iters); nullptr for ISTA
   const float2* twiddle;   // W_1024^e, e = 0..1023 (float2)
-  const float* mult;       // Fourier multipliers (include 1/(L1 L2)), natural order [p2][p1]
-  const float2* cterm;     // mu*b (ISTA/FISTA) or d = (G + rho I)^{-1} b (ADMM)
+  const float* mult;       // Fourier multiplier q (includes 1/(L1 L2)), natural order [p2][p1]
+  const float2* bt;        // Fourier-domain constant term Bt, natural order [p2][p1]
   const float2* c0;        // warm start (z^(0) for ADMM) or nullptr for zeros
   float2* c_out;           // c^(T) (ISTA/FISTA) or z^(T) (ADMM)
   float2* aux_out;         // ADMM only: c^(T); nullable
@@ -77,8 +83,8 @@ struct FusedShape {
   static constexpr int P = L1 + L1 / 16;                          // padded row pitch
   static constexpr int NMAX = cmax(L1, L2);
   static constexpr int SH = RP * L1 / C;                          // middle-stage pairs per CTA
-  static constexpr bool M_SMEM = !ADMM;                           // multiplier share in smem
-  static constexpr int SMEM = (R * P + E + (ADMM ? E : 0)) * 8 + (M_SMEM ? E * 4 : 0) + NMAX * 8;
+  // work (padded) + two state grids + a flag byte per owned frequency + twiddles
+  static constexpr int SMEM = (R * P + 2 * E) * 8 + E + NMAX * 8;
   static_assert(L1 >= 16 && L2 >= 16, "fused path needs L1, L2 >= 16");
   static_assert(C <= 8, "cluster larger than 8 CTAs");
   static_assert(QV * C == Q, "cluster size must divide the cross-group radix");
@@ -104,9 +110,9 @@ struct FusedCta {
   static constexpr int Q = S::Q, QV = S::QV, RP = S::RP, P = S::P, NMAX = S::NMAX, SH = S::SH;
 
   float2* work;        // R x P (padded)
-  float2* cst;         // E: c (ISTA/FISTA) or z (ADMM)
-  float2* vst;         // E: v (ADMM)
-  float* mloc;         // E: multiplier share (if in smem)
+  float2* s0;          // E: c (ISTA/FISTA) or z (ADMM)
+  float2* s1;          // E: z (FISTA) or v (ADMM)
+  uint8_t* flag;       // E: 1 where this CTA's middle-stage frequency has q != 0
   float2* tw;          // NMAX twiddles W_NMAX^e
   int crank;
   int tid;
@@ -213,7 +219,7 @@ struct FusedCta {
   // ---------------------------------------------------------------------------------------
   // cross-group radix-Q stage, Fourier multiplier, inverse radix-Q stage (in place)
   // ---------------------------------------------------------------------------------------
-  __device__ __forceinline__ void middle(float2* const* peer, const float* mult_g) {
+  __device__ __forceinline__ void middle(float2* const* peer, const float* mult_g, const float2* bt_g) {
     constexpr int PT = (SH + T - 1) / T;
 #pragma unroll
     for (int k = 0; k < PT; ++k) {
@@ -232,13 +238,14 @@ struct FusedCta {
         Dft<Q, false, float2>::run(v);
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-          float m;
-          if constexpr (S::M_SMEM) {
-            m = mloc[q * SH + pl];
+          if (flag[q * SH + pl]) {
+            const int f = (k1 + RP * q) * L1 + col;
+            const float m = __ldg(&mult_g[f]);
+            const float2 b = __ldg(&bt_g[f]);
+            v[q] = make_float2(v[q].x * m - b.x, v[q].y * m - b.y);
           } else {
-            m = __ldg(&mult_g[(k1 + RP * q) * L1 + col]);
+            v[q] = make_float2(0.f, 0.f);
           }
-          v[q] = make_float2(v[q].x * m, v[q].y * m);
         }
         Dft<Q, true, float2>::run(v);
 #pragma unroll
@@ -265,21 +272,13 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM>::T, 1)
   char* sp = reinterpret_cast<char*>(smem_raw);
   cta.work = reinterpret_cast<float2*>(sp);
   sp += R * P * 8;
-  cta.cst = reinterpret_cast<float2*>(sp);
+  cta.s0 = reinterpret_cast<float2*>(sp);
   sp += E * 8;
-  if constexpr (ADMM) {
-    cta.vst = reinterpret_cast<float2*>(sp);
-    sp += E * 8;
-  } else {
-    cta.vst = nullptr;
-  }
+  cta.s1 = reinterpret_cast<float2*>(sp);
+  sp += E * 8;
   cta.tw = reinterpret_cast<float2*>(sp);
   sp += NMAX * 8;
-  if constexpr (S::M_SMEM) {
-    cta.mloc = reinterpret_cast<float*>(sp);
-  } else {
-    cta.mloc = nullptr;
-  }
+  cta.flag = reinterpret_cast<uint8_t*>(sp);
   cta.tid = threadIdx.x;
   int crank = 0;
   if constexpr (C > 1) crank = (int)cg::this_cluster().block_rank();
@@ -289,7 +288,7 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM>::T, 1)
   const FusedInst in = a.insts[inst_id];
   const float kappa = in.kappa;
   const float* mult = a.mult + in.g_off;
-  const float2* cterm = a.cterm + in.g_off;
+  const float2* bt = a.bt + in.g_off;
   const float2* c0 = a.c0 ? a.c0 + in.c_off : nullptr;
   float2* c_out = a.c_out + in.c_off;
   float2* aux_out = a.aux_out ? a.aux_out + in.c_off : nullptr;
@@ -305,20 +304,19 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM>::T, 1)
 
   // ---- load twiddles, multiplier share, initial state
   for (int e = threadIdx.x; e < NMAX; e += T) cta.tw[e] = a.twiddle[e * (kTwiddleLen / NMAX)];
-  if constexpr (S::M_SMEM) {
-    for (int idx = threadIdx.x; idx < E; idx += T) {
-      const int q = idx / SH, pl = idx % SH;
-      const int p = crank * SH + pl;
-      const int k1 = p / L1, col = p % L1;
-      cta.mloc[idx] = mult[(k1 + RP * q) * L1 + col];
-    }
+  for (int idx = threadIdx.x; idx < E; idx += T) {
+    const int q = idx / SH, pl = idx % SH;
+    const int p = crank * SH + pl;
+    const int k1 = p / L1, col = p % L1;
+    const int f = (k1 + RP * q) * L1 + col;
+    cta.flag[idx] = (mult[f] != 0.f || bt[f].x != 0.f || bt[f].y != 0.f) ? 1 : 0;
   }
   for (int idx = threadIdx.x; idx < E; idx += T) {
     const int s = idx / L1, e = idx % L1;
     const int gidx = (crank + C * s) * L1 + e;
     float2 x = c0 ? c0[gidx] : make_float2(0.f, 0.f);
-    cta.cst[idx] = x;
-    if constexpr (ADMM) cta.vst[idx] = make_float2(0.f, 0.f);
+    cta.s0[idx] = x;                                        // c^(0) or z^(0)
+    cta.s1[idx] = ADMM ? make_float2(0.f, 0.f) : x;         // z^(1) = c^(0), or v^(0) = 0
     cta.work[s * P + pad16(e)] = x;
   }
   __syncthreads();
@@ -334,35 +332,35 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM>::T, 1)
     // forward local column DFTs
     cta.template col_fft_from<0, false>();
     if constexpr (C > 1) cg::this_cluster().sync(); else __syncthreads();
-    cta.middle(peer, mult);
+    cta.middle(peer, mult, bt);
     if constexpr (C > 1) cg::this_cluster().sync(); else __syncthreads();
     cta.template col_fft_from<0, true>();
     // inverse row DFTs with the fused epilogue
-    cta.template row_fft_from<0, true>([&](int row, int e, float2 u) {
+    cta.template row_fft_from<0, true>([&](int row, int e, float2 g) {
       const int sidx = row * L1 + e;
-      const int gidx = (crank + C * row) * L1 + e;
-      const float2 ct = __ldg(&cterm[gidx]);
       if constexpr (!ADMM) {
-        const float2 un = make_float2(u.x + ct.x, u.y + ct.y);
+        const float2 c_old = cta.s0[sidx];
+        const float2 x = fista ? cta.s1[sidx] : c_old;  // z^(t)
+        const float2 un = make_float2(x.x - g.x, x.y - g.y);
         const float2 cn = soft_threshold(un, kappa);
-        float2 z = cn;
+        cta.s0[sidx] = cn;
         if (fista) {
-          const float2 co = cta.cst[sidx];
-          z = make_float2(cn.x + beta * (cn.x - co.x), cn.y + beta * (cn.y - co.y));
+          const float2 zn = make_float2(cn.x + beta * (cn.x - c_old.x), cn.y + beta * (cn.y - c_old.y));
+          cta.s1[sidx] = zn;
+          cta.work[row * P + pad16(e)] = zn;
+        } else {
+          cta.work[row * P + pad16(e)] = cn;
         }
-        cta.cst[sidx] = cn;
-        cta.work[row * P + pad16(e)] = z;
       } else {
-        const float2 cc = make_float2(u.x + ct.x, u.y + ct.y);
-        const float2 zo = cta.cst[sidx];
-        (void)zo;
-        const float2 vo = cta.vst[sidx];
-        const float2 zn = soft_threshold(make_float2(cc.x + vo.x, cc.y + vo.y), kappa);
-        const float2 vn = make_float2(vo.x + cc.x - zn.x, vo.y + cc.y - zn.y);
-        cta.cst[sidx] = zn;
-        cta.vst[sidx] = vn;
+        const float2 zo = cta.s0[sidx];
+        const float2 vo = cta.s1[sidx];
+        const float2 un = make_float2(zo.x - g.x, zo.y - g.y);  // c^(t+1) + v^(t)
+        const float2 zn = soft_threshold(un, kappa);
+        const float2 vn = make_float2(un.x - zn.x, un.y - zn.y);
+        cta.s0[sidx] = zn;
+        cta.s1[sidx] = vn;
         cta.work[row * P + pad16(e)] = make_float2(zn.x - vn.x, zn.y - vn.y);
-        if (last && aux_out) aux_out[gidx] = cc;
+        if (last && aux_out) aux_out[(crank + C * row) * L1 + e] = make_float2(un.x - vo.x, un.y - vo.y);
       }
     });
   }
@@ -370,7 +368,7 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM>::T, 1)
   // ---- write the result
   for (int idx = threadIdx.x; idx < E; idx += T) {
     const int s = idx / L1, e = idx % L1;
-    c_out[(crank + C * s) * L1 + e] = cta.cst[idx];
+    c_out[(crank + C * s) * L1 + e] = cta.s0[idx];
   }
   if constexpr (C > 1) cg::this_cluster().sync();
 }

@@ -7,8 +7,10 @@
 //   * b = A^H y: with gamma = 1/2 the dictionary entry is (-1)^(m1+m2) times a DFT
 //     kernel, so b is the unnormalised inverse 2D DFT of the grid holding
 //     (-1)^(m1+m2) y_n at (m1 mod L1, m2 mod L2) (eq:ista, eq:admm).
-//   * ADMM's precomputed term d = (A^H A + rho I)^{-1} b, applied in the Fourier domain
-//     as IFFT2(FFT2(b)/(Lambda + rho)) (eq:admm, Section III-B).
+//   * the FP32 Fourier multiplier q and the Fourier-domain constant term Bt used by the
+//     fused iterations: FFT2(b) is L1 L2 times the signed measurement grid, so Bt needs
+//     no transform; for ADMM it carries the "precomputed" (A^H A + rho I)^{-1} A^H y of
+//     eq:admm as FFT2(b)/(Lambda + rho).
 //   * the final check: r = A^H (y - A c) = b - G c, the relative KKT residual of the
 //     1/2-scaled LASSO, and the objective 1/2 ||y - A c||^2 + lam ||c||_1.
 // The FP64 2D DFTs are plain radix-2 Stockham passes (rows, then columns) over
@@ -138,78 +140,65 @@ struct SumOp {
   __device__ double operator()(double a, double b) const { return a + b; }
 };
 
-// Lambda, mu, lam, kappa, the FP32 multiplier and (ISTA/FISTA) the constant term mu*b.
-__global__ void eig_params_kernel(const InstDesc* __restrict__ desc, const double2* __restrict__ lam_c,
-                                  const double2* __restrict__ b64, double* lam64, InstParams* par,
-                                  float* mult, float2* cterm, FusedInst* fused, int algo, double rho) {
+// Lambda (real part of the FFT2 of the Gram's first column), mu = 1/max Lambda, the FP32
+// Fourier multiplier q and the FP32 Fourier-domain constant term Bt (both include the
+// 1/(L1 L2) of the unnormalised inverse DFT):
+//   ISTA/FISTA: q = mu Lambda / L,          Bt = mu * FFT2(b) / L = mu * s
+//   ADMM:       q = Lambda/(Lambda+rho)/L,  Bt = FFT2(b) / (Lambda + rho) / L = s / (Lambda + rho)
+// where s is the signed, folded measurement grid (FFT2(b) = L * s because b is the
+// unnormalised inverse DFT of s).  Entries of Lambda below 1e-9 max Lambda are the
+// round-off of the FP64 DFTs of an exactly zero eigenvalue and are set to 0.
+__global__ void eig_mult_kernel(const InstDesc* __restrict__ desc, const double2* __restrict__ lam_c,
+                                const double2* __restrict__ sgrid, double* lam64, InstParams* par, float* mult,
+                                float2* bt, int algo, double rho) {
   __shared__ double sh[32];
   const InstDesc d = desc[blockIdx.x];
   const int L = d.L1 * d.L2;
-  double top = 0.0, bmax = 0.0;
+  double top = 0.0;
+  for (int cell = threadIdx.x; cell < L; cell += blockDim.x) top = fmax(top, lam_c[d.g_off + cell].x);
+  top = block_reduce(top, MaxOp(), sh, 0.0);
+  const double mu = 1.0 / top;
+  const double inv_L = 1.0 / (double)L;
   for (int cell = threadIdx.x; cell < L; cell += blockDim.x) {
-    const double lv = lam_c[d.g_off + cell].x;
+    double lv = lam_c[d.g_off + cell].x;
+    if (lv < 1e-9 * top) lv = 0.0;
     lam64[d.g_off + cell] = lv;
-    top = fmax(top, lv);
+    const double2 sv = sgrid[d.g_off + cell];
+    double m, bs;
+    if (algo == 2) {
+      m = lv / (lv + rho) * inv_L;
+      bs = 1.0 / (lv + rho);
+    } else {
+      m = mu * lv * inv_L;
+      bs = mu;
+    }
+    mult[d.g_off + cell] = (float)m;
+    bt[d.g_off + cell] = make_float2((float)(sv.x * bs), (float)(sv.y * bs));
+  }
+  if (threadIdx.x == 0) {
+    par[blockIdx.x].mu = mu;
+    par[blockIdx.x].lam_top = top;
+  }
+}
+
+// lam (absolute, or a fraction of ||A^H y||_inf) and the soft-threshold kappa
+__global__ void lam_kappa_kernel(const InstDesc* __restrict__ desc, const double2* __restrict__ b64,
+                                 InstParams* par, FusedInst* fused, int algo, double rho) {
+  __shared__ double sh[32];
+  const InstDesc d = desc[blockIdx.x];
+  const int L = d.L1 * d.L2;
+  double bmax = 0.0;
+  for (int cell = threadIdx.x; cell < L; cell += blockDim.x) {
     const double2 bv = b64[d.g_off + cell];
     bmax = fmax(bmax, sqrt(bv.x * bv.x + bv.y * bv.y));
   }
-  top = block_reduce(top, MaxOp(), sh, 0.0);
   bmax = block_reduce(bmax, MaxOp(), sh, 0.0);
-  const double mu = 1.0 / top;
-  const double lam = d.lam_is_frac ? d.lam * bmax : d.lam;
-  const double inv_L = 1.0 / (double)L;
-  for (int cell = threadIdx.x; cell < L; cell += blockDim.x) {
-    const double lv = lam64[d.g_off + cell];
-    double m;
-    if (algo == 2) {
-      m = rho / (lv + rho) * inv_L;
-    } else {
-      m = (1.0 - mu * lv) * inv_L;
-      const double2 bv = b64[d.g_off + cell];
-      cterm[d.g_off + cell] = make_float2((float)(mu * bv.x), (float)(mu * bv.y));
-    }
-    mult[d.g_off + cell] = (float)m;
-  }
   if (threadIdx.x == 0) {
-    InstParams p;
-    p.mu = mu;
-    p.lam = lam;
-    p.lmax = bmax;
-    p.lam_top = top;
-    par[blockIdx.x] = p;
+    const double mu = par[blockIdx.x].mu;
+    const double lam = d.lam_is_frac ? d.lam * bmax : d.lam;
+    par[blockIdx.x].lam = lam;
+    par[blockIdx.x].lmax = bmax;
     fused[blockIdx.x].kappa = (float)(algo == 2 ? lam / rho : mu * lam);
-  }
-}
-
-__global__ void copy_grid_kernel(const InstDesc* __restrict__ desc, const double2* __restrict__ src,
-                                 double2* dst) {
-  const InstDesc d = desc[blockIdx.x];
-  const int L = d.L1 * d.L2;
-  for (int cell = blockIdx.y * blockDim.x + threadIdx.x; cell < L; cell += gridDim.y * blockDim.x)
-    dst[d.g_off + cell] = src[d.g_off + cell];
-}
-
-// w <- w / (Lambda + rho)
-__global__ void admm_divide_kernel(const InstDesc* __restrict__ desc, const double* __restrict__ lam64,
-                                   double2* w, double rho) {
-  const InstDesc d = desc[blockIdx.x];
-  const int L = d.L1 * d.L2;
-  for (int cell = blockIdx.y * blockDim.x + threadIdx.x; cell < L; cell += gridDim.y * blockDim.x) {
-    const double s = 1.0 / (lam64[d.g_off + cell] + rho);
-    const double2 v = w[d.g_off + cell];
-    w[d.g_off + cell] = make_double2(v.x * s, v.y * s);
-  }
-}
-
-// cterm <- w / (L1 L2)  (normalises the inverse DFT)
-__global__ void cterm_from_w_kernel(const InstDesc* __restrict__ desc, const double2* __restrict__ w,
-                                    float2* cterm) {
-  const InstDesc d = desc[blockIdx.x];
-  const int L = d.L1 * d.L2;
-  const double s = 1.0 / (double)L;
-  for (int cell = blockIdx.y * blockDim.x + threadIdx.x; cell < L; cell += gridDim.y * blockDim.x) {
-    const double2 v = w[d.g_off + cell];
-    cterm[d.g_off + cell] = make_float2((float)(v.x * s), (float)(v.y * s));
   }
 }
 
@@ -357,21 +346,16 @@ cudaError_t fista_schedule(bccb_solver* s, int iters) {
 
 cudaError_t run_setup(bccb_solver* s, const float2* y_dev) {
   const dim3 gc = grid_cells(s);
+  // count grid -> d_w64, signed measurement grid s -> d_b64
   scatter_kernel<<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_mask_idx, y_dev, s->d_w64, s->d_b64);
-  s->launches += 2 + (s->algo == 2 ? 3 : 0);  // scatter, eig_params (+ copy, divide, cterm)
+  s->launches += 3;  // scatter, eig_mult, lam_kappa
   cudaError_t err;
   if ((err = fft2_64(s, s->d_w64, 1)) != cudaSuccess) return err;  // first column of the Gram
-  if ((err = fft2_64(s, s->d_b64, 1)) != cudaSuccess) return err;  // b = A^H y
   if ((err = fft2_64(s, s->d_w64, 0)) != cudaSuccess) return err;  // Lambda (eq:lambda)
-  eig_params_kernel<<<s->n, kThreads, 0, s->stream>>>(s->d_desc, s->d_w64, s->d_b64, s->d_lam64, s->d_par,
-                                                       s->d_mult, s->d_cterm, s->d_fused, s->algo, s->rho);
-  if (s->algo == 2) {
-    copy_grid_kernel<<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_b64, s->d_w64);
-    if ((err = fft2_64(s, s->d_w64, 0)) != cudaSuccess) return err;
-    admm_divide_kernel<<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_lam64, s->d_w64, s->rho);
-    if ((err = fft2_64(s, s->d_w64, 1)) != cudaSuccess) return err;
-    cterm_from_w_kernel<<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_w64, s->d_cterm);
-  }
+  eig_mult_kernel<<<s->n, kThreads, 0, s->stream>>>(s->d_desc, s->d_w64, s->d_b64, s->d_lam64, s->d_par,
+                                                     s->d_mult, s->d_cterm, s->algo, s->rho);
+  if ((err = fft2_64(s, s->d_b64, 1)) != cudaSuccess) return err;  // b = A^H y
+  lam_kappa_kernel<<<s->n, kThreads, 0, s->stream>>>(s->d_desc, s->d_b64, s->d_par, s->d_fused, s->algo, s->rho);
   return cudaGetLastError();
 }
 

@@ -59,7 +59,7 @@ struct bccb_solver {
   double2* d_b64 = nullptr;     // b = A^H y (FP64)
   double2* d_w64 = nullptr;     // FP64 FFT workspace
   float* d_mult = nullptr;      // FP32 Fourier multiplier (includes 1/(L1 L2))
-  float2* d_cterm = nullptr;    // FP32 mu*b or d
+  float2* d_cterm = nullptr;    // FP32 Fourier-domain constant term Bt
   bccb::InstParams* d_par = nullptr;
   bccb::FusedInst* d_fused = nullptr;
   int* d_ids = nullptr;

@@ -74,15 +74,20 @@ def test_fista_64x64_500_iterations(lib):
     assert run["res"]["kkt"][0] == pytest.approx(oracle.kkt_residual(ref["A"], s.y, run["c"][0].astype(np.complex128), ref["lam"]), abs=1e-4)
 
 
-@pytest.mark.parametrize("algo", ["ista", "fista", "admm"])
-def test_256x256_1000_iterations(lib, algo):
-    """32x32 array, N=256, 256x256 grid, 8 off-grid sources, 10 dB, 1000 iterations (ADMM rho=1)."""
+@pytest.mark.parametrize("algo,rho", [("ista", 1.0), ("fista", 1.0), ("admm", 1.0), ("admm", 256.0)])
+def test_256x256_1000_iterations(lib, algo, rho):
+    """32x32 array, N=256, 256x256 grid, 8 off-grid sources, 10 dB, 1000 iterations (ADMM with
+    rho = 1 as specified, and with rho = 256 = N, where ADMM actually moves z off 0)."""
     s = synth.config_snapshot(2, 0)
-    ref = oracle_run(s, algo, 1000, rho=1.0)
-    run = gpu_run(lib, [s], [ref["lam"]], algo, 1000, rho=1.0)
-    assert_parity(run["c"][0], ref, what=f"{algo} 256x256")
+    ref = oracle_run(s, algo, 1000, rho=rho)
+    run = gpu_run(lib, [s], [ref["lam"]], algo, 1000, rho=rho)
+    assert_parity(run["c"][0], ref, what=f"{algo} 256x256 rho={rho}")
     if algo == "admm":
-        assert_parity(run["aux"][0], ref, ref_c=ref["aux"], what="admm c^(T)")
+        # c^(T) = u - v^(T-1) with |u| ~ |v|; at rho = 1 ||v||/||c|| is about T, so FP32 keeps
+        # log2(T) fewer bits of c than of u and v: allow 16 ulps of ||v|| relative to ||c||.
+        ratio = np.linalg.norm(ref["u"] - ref["aux"]) / np.linalg.norm(ref["aux"])
+        tol = max(1e-4, 16 * 2.0**-24 * ratio)
+        assert_parity(run["aux"][0], ref, ref_c=ref["aux"], tol=tol, what=f"admm c^(T) rho={rho} tol={tol:.1e}")
 
 
 # ------------------------------------------------------------------------------------------
