@@ -137,6 +137,34 @@ int bccb_batch_size(bccb_solver_t s, int* n);
 int bccb_instance_shape(bccb_solver_t s, int i, int* L1, int* L2, int* N);
 
 int bccb_destroy(bccb_solver_t s);
+
+/* Solve one instance without allocating any device memory.
+ *
+ * For callers that cannot call cudaMalloc: code running where the device
+ * allocator is off limits (a host process whose memory budget is fixed up
+ * front, a plugin inside another runtime that owns all allocations, or a path
+ * that must not risk an allocation failure or the implicit synchronisation an
+ * allocation can bring).  The paper has no counterpart; this is a deployment
+ * convenience over the same kernels as bccb_solve.
+ *
+ * All working memory (about 3.4 MB) is one fixed array compiled into the
+ * library, which every GPU that loads the library holds until the process
+ * exits.  The first call on each device looks that array up and uploads the
+ * twiddle tables (make that first call before any stream capture); later calls
+ * do no set-up.  Every call on a device reuses the same array: calls whose work
+ * overlaps on the GPU (two streams, or two threads) race and corrupt each other,
+ * so serialise them.  Each call rewrites every part of the array it reads, so
+ * nothing left by an earlier call leaks into a result.
+ *
+ * Arguments as for bccb_create + bccb_solve, except that the mask is a DEVICE
+ * pointer (uint8, M1*M2) and there is no KKT check.  Limits: L1, L2 powers of
+ * two in [16, 256] (L1*L2 <= 65536), M1*M2 <= 16384, 1 <= iters <= 8192; larger
+ * sizes return BCCB_ERR_UNSUPPORTED before any work is queued.  Asynchronous on
+ * cuda_stream; y_dev and c_out_dev as for bccb_solve (c_out receives c^(T), or
+ * z^(T) for ADMM). */
+int bccb_solve_noalloc(int M1, int M2, const uint8_t* mask_dev, int L1, int L2, int algo, double rho,
+                       const void* y_dev, double lam, int lam_is_frac, int iters, void* c_out_dev,
+                       void* cuda_stream);
 const char* bccb_status_string(int status);
 /* Message for the solver's last failure ("" if none); s may be NULL for create errors. */
 const char* bccb_last_error(bccb_solver_t s);

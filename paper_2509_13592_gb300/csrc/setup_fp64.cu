@@ -373,4 +373,9 @@ cudaError_t run_check(bccb_solver* s, const float2* y_dev, const float2* c_dev) 
   return cudaGetLastError();
 }
 
+cudaError_t prepare_fp64_passes(int max_L2) {
+  const int col_smem = 2 * max_L2 * kColsPerBlock * (int)sizeof(double2);
+  return cudaFuncSetAttribute(fft64_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem);
+}
+
 }  // namespace bccb

@@ -89,6 +89,8 @@ cudaError_t run_setup(bccb_solver* s, const float2* y_dev);
 cudaError_t run_check(bccb_solver* s, const float2* y_dev, const float2* c_dev);
 cudaError_t fill_twiddles(bccb_solver* s);
 cudaError_t fista_schedule(bccb_solver* s, int iters);
+// shared-memory opt-in of the FP64 column pass for grids with up to max_L2 rows
+cudaError_t prepare_fp64_passes(int max_L2);
 // fused_L*.cu
 const FusedEntry* fused_lookup(int L1, int L2, bool admm);
 }  // namespace bccb
