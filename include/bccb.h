@@ -124,6 +124,24 @@ int bccb_create(bccb_solver_t* out, int M1, int M2, const uint8_t* mask_host, in
 int bccb_solve(bccb_solver_t s, const void* y_dev, double lam, int lam_is_frac, int iters, const void* c0_dev,
                void* c_out_dev, void* aux_out_dev, double* kkt_out, double* obj_out);
 
+/* Capture the whole of bccb_batch_solve (same arguments) into a CUDA graph on the
+ * solver's stream, which must not be the legacy default stream; bccb_batch_replay
+ * launches it again (same buffers, same iteration count).  A later capture or
+ * bccb_batch_tune replaces it.  The multi-class launch is a fork/join over one
+ * stream per (L1, L2) class, so the classes of a ragged batch run concurrently. */
+int bccb_batch_capture(bccb_solver_t s, const void* y_dev, int iters, const void* c0_dev, void* c_out_dev,
+                       void* aux_out_dev, int check);
+int bccb_batch_replay(bccb_solver_t s);
+
+/* Autotuner: for every (L1, L2) class of the batch, time each fused-kernel tile
+ * (8192 grid elements per CTA, or 4096 = twice the CTAs per cluster, two CTAs per
+ * SM) for probe_iters iterations on the class's own instances, after one setup with
+ * y_dev, and keep the fastest.  cache_path (nullable): a text file of lines
+ * "gpu_name L1 L2 admm tile"; classes found there for this GPU are not measured,
+ * new choices are appended.  Synchronises.  bccb_batch_tile reports the choice. */
+int bccb_batch_tune(bccb_solver_t s, const void* y_dev, int probe_iters, const char* cache_path);
+int bccb_batch_tile(bccb_solver_t s, int L1, int L2, int* tile);
+
 /* Phase timing of bccb_batch_solve, for profiling.  bccb_set_timing(s, 1) makes
  * every later solve record CUDA events on the solver's stream around its three
  * phases; bccb_last_timing synchronises and returns the last solve's setup,

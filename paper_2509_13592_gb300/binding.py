@@ -54,6 +54,10 @@ def _load():
     lib.bccb_set_timing.argtypes = [vp, i32]
     lib.bccb_last_timing.argtypes = [vp, P(ctypes.c_float), P(ctypes.c_float), P(ctypes.c_float),
                                      P(ctypes.c_int64)]
+    lib.bccb_batch_capture.argtypes = [vp, vp, i32, vp, vp, vp, i32]
+    lib.bccb_batch_replay.argtypes = [vp]
+    lib.bccb_batch_tune.argtypes = [vp, vp, i32, ctypes.c_char_p]
+    lib.bccb_batch_tile.argtypes = [vp, i32, i32, P(i32)]
     lib.bccb_batch_size.argtypes = [vp, P(i32)]
     lib.bccb_instance_shape.argtypes = [vp, i32, P(i32), P(i32), P(i32)]
     lib.bccb_destroy.argtypes = [vp]
@@ -63,7 +67,8 @@ def _load():
     lib.bccb_last_error.restype = ctypes.c_char_p
     for name in ("bccb_batch_create", "bccb_batch_solve", "bccb_batch_solve_host", "bccb_batch_results",
                  "bccb_batch_get", "bccb_create", "bccb_solve", "bccb_batch_size", "bccb_instance_shape",
-                 "bccb_destroy", "bccb_set_timing", "bccb_last_timing"):
+                 "bccb_destroy", "bccb_set_timing", "bccb_last_timing", "bccb_batch_capture", "bccb_batch_replay",
+                 "bccb_batch_tune", "bccb_batch_tile"):
         getattr(lib, name).restype = i32
     return lib
 
@@ -157,6 +162,26 @@ def bccb_solve(h: int, y_dev, lam: float, lam_is_frac: bool, iters: int, c0_dev,
                          ctypes.byref(obj) if check else None)
     _raise(st, h)
     return (kkt.value, obj.value) if check else None
+
+
+def bccb_batch_capture(h: int, y_dev, iters: int, c0_dev, c_out_dev, aux_out_dev=None, check: bool = True) -> None:
+    _raise(_lib.bccb_batch_capture(h, _ptr(y_dev), int(iters), _ptr(c0_dev), _ptr(c_out_dev), _ptr(aux_out_dev),
+                                   1 if check else 0), h)
+
+
+def bccb_batch_replay(h: int) -> None:
+    _raise(_lib.bccb_batch_replay(h), h)
+
+
+def bccb_batch_tune(h: int, y_dev, probe_iters: int = 20, cache_path: Optional[str] = None) -> None:
+    _raise(_lib.bccb_batch_tune(h, _ptr(y_dev), int(probe_iters),
+                                None if cache_path is None else cache_path.encode()), h)
+
+
+def bccb_batch_tile(h: int, L1: int, L2: int) -> int:
+    t = ctypes.c_int(0)
+    _raise(_lib.bccb_batch_tile(h, int(L1), int(L2), ctypes.byref(t)), h)
+    return t.value
 
 
 def bccb_set_timing(h: int, enable: bool) -> None:

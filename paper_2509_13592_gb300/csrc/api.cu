@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <map>
+#include <tuple>
 #include <string>
 #include <utility>
 #include <vector>
@@ -43,7 +44,21 @@ cudaError_t dalloc(T** p, size_t count) {
   return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
 }
 
+void release_streams(bccb_solver* s) {
+  for (cudaStream_t st : s->class_streams) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : s->class_done) cudaEventDestroy(ev);
+  if (s->fork) cudaEventDestroy(s->fork);
+  if (s->graph) cudaGraphExecDestroy(s->graph);
+  if (s->d_probe) cudaFree(s->d_probe);
+  s->class_streams.clear();
+  s->class_done.clear();
+  s->fork = nullptr;
+  s->graph = nullptr;
+  s->d_probe = nullptr;
+}
+
 void release(bccb_solver* s) {
+  release_streams(s);
   void* ptrs[] = {s->d_desc, s->d_mask_idx, s->d_lam64, s->d_b64,  s->d_w64,    s->d_mult,    s->d_cterm,
                   s->d_par,  s->d_fused,    s->d_ids,   s->d_beta, s->d_kkt,    s->d_obj,     s->d_red,
                   s->d_tw32, s->d_tw64,     s->d_y_stage, s->d_c_stage};
@@ -133,7 +148,7 @@ int bccb_batch_create(bccb_solver_t* out, const bccb_inst_t* insts, int n, const
     fused[i].g_off = g_off;
     fused[i].c_off = q.c_off;
     fused[i].kappa = 0.f;
-    fused[i].pad_ = 0;
+    fused[i].kcols = q.L1;
     by_shape[{q.L1, q.L2}].push_back(i);
     mm_off += (int64_t)q.M1 * q.M2;
     g_off += (int64_t)q.L1 * q.L2;
@@ -192,6 +207,17 @@ int bccb_batch_create(bccb_solver_t* out, const bccb_inst_t* insts, int n, const
   CREATE_CUDA(cudaMemcpy(s->d_ids, ids.data(), n * sizeof(int), cudaMemcpyHostToDevice));
   CREATE_CUDA(bccb::fill_twiddles(s));
   for (auto& c : s->classes) CREATE_CUDA(c.entry.prepare());
+  if (s->classes.size() > 1) {
+    CREATE_CUDA(cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming));
+    for (size_t k = 0; k < s->classes.size(); ++k) {
+      cudaStream_t st;
+      cudaEvent_t ev;
+      CREATE_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+      s->class_streams.push_back(st);
+      CREATE_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      s->class_done.push_back(ev);
+    }
+  }
 #undef CREATE_CUDA
   *out = s;
   return BCCB_OK;
@@ -205,11 +231,11 @@ int bccb_batch_solve(bccb_solver_t s, const void* y_dev, int iters, const void* 
   if (iters < 1) return fail(s, BCCB_ERR_INVALID_ARG, "iters must be >= 1");
   BCCB_CUDA(s, cudaSetDevice(s->device));
   s->launches = 0;
-  if (s->timing) BCCB_CUDA(s, cudaEventRecord(s->ev[0], s->stream));
+  if (s->timing) BCCB_CUDA(s, cudaEventRecordWithFlags(s->ev[0], s->stream, cudaEventRecordExternal));
   if (s->algo == BCCB_FISTA) BCCB_CUDA(s, bccb::fista_schedule(s, iters));
   const float2* y = reinterpret_cast<const float2*>(y_dev);
   BCCB_CUDA(s, bccb::run_setup(s, y));
-  if (s->timing) BCCB_CUDA(s, cudaEventRecord(s->ev[1], s->stream));
+  if (s->timing) BCCB_CUDA(s, cudaEventRecordWithFlags(s->ev[1], s->stream, cudaEventRecordExternal));
   FusedArgs a;
   a.insts = s->d_fused;
   a.beta = (s->algo == BCCB_FISTA) ? s->d_beta : nullptr;
@@ -221,14 +247,26 @@ int bccb_batch_solve(bccb_solver_t s, const void* y_dev, int iters, const void* 
   a.aux_out = (s->algo == BCCB_ADMM) ? reinterpret_cast<float2*>(aux_out_dev) : nullptr;
   a.iters = iters;
   a.pad_ = 0;
-  for (const auto& c : s->classes) {
-    a.ids = s->d_ids + c.first;
-    BCCB_CUDA(s, c.entry.launch(a, c.count, s->stream));
+  if (s->classes.size() == 1) {
+    a.ids = s->d_ids;
+    BCCB_CUDA(s, s->classes[0].entry.launch(a, s->classes[0].count, s->stream));
     s->launches += 1;
+  } else {
+    // one stream per shape class, forked from and joined back to the solver's stream
+    BCCB_CUDA(s, cudaEventRecord(s->fork, s->stream));
+    for (size_t k = 0; k < s->classes.size(); ++k) {
+      const auto& c = s->classes[k];
+      a.ids = s->d_ids + c.first;
+      BCCB_CUDA(s, cudaStreamWaitEvent(s->class_streams[k], s->fork, 0));
+      BCCB_CUDA(s, c.entry.launch(a, c.count, s->class_streams[k]));
+      BCCB_CUDA(s, cudaEventRecord(s->class_done[k], s->class_streams[k]));
+      BCCB_CUDA(s, cudaStreamWaitEvent(s->stream, s->class_done[k], 0));
+      s->launches += 1;
+    }
   }
-  if (s->timing) BCCB_CUDA(s, cudaEventRecord(s->ev[2], s->stream));
+  if (s->timing) BCCB_CUDA(s, cudaEventRecordWithFlags(s->ev[2], s->stream, cudaEventRecordExternal));
   if (check) BCCB_CUDA(s, bccb::run_check(s, y, reinterpret_cast<const float2*>(c_out_dev)));
-  if (s->timing) BCCB_CUDA(s, cudaEventRecord(s->ev[3], s->stream));
+  if (s->timing) BCCB_CUDA(s, cudaEventRecordWithFlags(s->ev[3], s->stream, cudaEventRecordExternal));
   s->last_checked = check != 0;
   return BCCB_OK;
 }
@@ -334,6 +372,142 @@ int bccb_last_timing(bccb_solver_t s, float* setup_ms, float* iterate_ms, float*
   if (iterate_ms) *iterate_ms = t[1];
   if (check_ms) *check_ms = s->last_checked ? t[2] : 0.f;
   if (launches) *launches = s->launches;
+  return BCCB_OK;
+}
+
+int bccb_batch_capture(bccb_solver_t s, const void* y_dev, int iters, const void* c0_dev, void* c_out_dev,
+                       void* aux_out_dev, int check) {
+  if (!s) return fail(nullptr, BCCB_ERR_INVALID_ARG, "solver is NULL");
+  if (!y_dev || !c_out_dev || iters < 1) return fail(s, BCCB_ERR_INVALID_ARG, "bad y, c_out or iters");
+  BCCB_CUDA(s, cudaSetDevice(s->device));
+  if (s->stream == nullptr)
+    return fail(s, BCCB_ERR_INVALID_ARG, "graph capture needs a non-default stream");
+  // anything that may allocate happens before the capture
+  if (s->algo == BCCB_FISTA) BCCB_CUDA(s, bccb::fista_schedule(s, iters));
+  BCCB_CUDA(s, cudaStreamSynchronize(s->stream));
+  if (s->graph) {
+    cudaGraphExecDestroy(s->graph);
+    s->graph = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  BCCB_CUDA(s, cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+  const int st = bccb_batch_solve(s, y_dev, iters, c0_dev, c_out_dev, aux_out_dev, check);
+  cudaError_t e = cudaStreamEndCapture(s->stream, &g);
+  if (st != BCCB_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(s, BCCB_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&s->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(s, BCCB_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  return BCCB_OK;
+}
+
+int bccb_batch_replay(bccb_solver_t s) {
+  if (!s) return fail(nullptr, BCCB_ERR_INVALID_ARG, "solver is NULL");
+  if (!s->graph) return fail(s, BCCB_ERR_INVALID_ARG, "no captured solve (call bccb_batch_capture first)");
+  BCCB_CUDA(s, cudaSetDevice(s->device));
+  BCCB_CUDA(s, cudaGraphLaunch(s->graph, s->stream));
+  return BCCB_OK;
+}
+
+int bccb_batch_tune(bccb_solver_t s, const void* y_dev, int probe_iters, const char* cache_path) {
+  if (!s) return fail(nullptr, BCCB_ERR_INVALID_ARG, "solver is NULL");
+  if (!y_dev || probe_iters < 1) return fail(s, BCCB_ERR_INVALID_ARG, "bad y or probe_iters");
+  BCCB_CUDA(s, cudaSetDevice(s->device));
+  cudaDeviceProp prop;
+  BCCB_CUDA(s, cudaGetDeviceProperties(&prop, s->device));
+  std::string gpu(prop.name);
+  for (char& ch : gpu)
+    if (ch == ' ') ch = '_';
+  // cached choices: lines "gpu L1 L2 admm tile"
+  std::map<std::tuple<int, int, int>, int> cached;
+  if (cache_path) {
+    if (FILE* f = fopen(cache_path, "r")) {
+      char name[256];
+      int l1, l2, ad, tile;
+      while (fscanf(f, "%255s %d %d %d %d", name, &l1, &l2, &ad, &tile) == 5)
+        if (gpu == name) cached[std::make_tuple(l1, l2, ad)] = tile;
+      fclose(f);
+    }
+  }
+  const int admm = s->algo == BCCB_ADMM ? 1 : 0;
+  bool need_probe = false;
+  for (auto& c : s->classes)
+    if (!cached.count(std::make_tuple(c.entry.L1, c.entry.L2, admm))) need_probe = true;
+  FILE* out = nullptr;
+  if (need_probe) {
+    if (s->algo == BCCB_FISTA) BCCB_CUDA(s, bccb::fista_schedule(s, probe_iters));
+    if (!s->d_probe) BCCB_CUDA(s, dalloc(&s->d_probe, s->total_c));
+    BCCB_CUDA(s, bccb::run_setup(s, reinterpret_cast<const float2*>(y_dev)));
+    if (cache_path) out = fopen(cache_path, "a");
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (need_probe) {
+    BCCB_CUDA(s, cudaEventCreate(&e0));
+    BCCB_CUDA(s, cudaEventCreate(&e1));
+  }
+  int status = BCCB_OK;
+  for (auto& c : s->classes) {
+    const auto key = std::make_tuple(c.entry.L1, c.entry.L2, admm);
+    auto it = cached.find(key);
+    if (it != cached.end()) {
+      if (const bccb::FusedEntry* fe = bccb::fused_lookup(c.entry.L1, c.entry.L2, admm != 0, it->second)) {
+        c.entry = *fe;
+        if (c.entry.prepare() != cudaSuccess) status = BCCB_ERR_CUDA;
+        continue;
+      }
+    }
+    FusedArgs a;
+    a.insts = s->d_fused;
+    a.ids = s->d_ids + c.first;
+    a.beta = (s->algo == BCCB_FISTA) ? s->d_beta : nullptr;
+    a.twiddle = s->d_tw32;
+    a.mult = s->d_mult;
+    a.bt = s->d_cterm;
+    a.c0 = nullptr;
+    a.c_out = s->d_probe;
+    a.aux_out = nullptr;
+    a.iters = probe_iters;
+    a.pad_ = 0;
+    float best = 1e30f;
+    bccb::FusedEntry best_e = c.entry;
+    for (int tile : {8192, 4096}) {
+      const bccb::FusedEntry* fe = bccb::fused_lookup(c.entry.L1, c.entry.L2, admm != 0, tile);
+      if (!fe || fe->prepare() != cudaSuccess) continue;
+      float ms = 0.f;
+      bool ok = fe->launch(a, c.count, s->stream) == cudaSuccess;  // warm-up
+      ok = ok && cudaEventRecord(e0, s->stream) == cudaSuccess;
+      ok = ok && fe->launch(a, c.count, s->stream) == cudaSuccess;
+      ok = ok && cudaEventRecord(e1, s->stream) == cudaSuccess;
+      ok = ok && cudaEventSynchronize(e1) == cudaSuccess;
+      ok = ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+      if (ok && ms < best) {
+        best = ms;
+        best_e = *fe;
+      }
+    }
+    c.entry = best_e;
+    if (out) fprintf(out, "%s %d %d %d %d\n", gpu.c_str(), c.entry.L1, c.entry.L2, admm, c.entry.tile);
+  }
+  if (out) fclose(out);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  BCCB_CUDA(s, cudaGetLastError());
+  if (s->graph) {  // a captured solve would still launch the old kernels
+    cudaGraphExecDestroy(s->graph);
+    s->graph = nullptr;
+  }
+  if (status != BCCB_OK) return fail(s, status, "preparing a cached tile failed");
+  return BCCB_OK;
+}
+
+int bccb_batch_tile(bccb_solver_t s, int L1, int L2, int* tile) {
+  if (!s || !tile) return fail(s, BCCB_ERR_INVALID_ARG, "NULL argument");
+  *tile = 0;
+  for (const auto& c : s->classes)
+    if (c.entry.L1 == L1 && c.entry.L2 == L2) *tile = c.entry.tile;
   return BCCB_OK;
 }
 

@@ -3,19 +3,20 @@
 
 namespace bccb {
 
-const FusedEntry* fused_lookup_L2_16(int L1, bool admm);
-const FusedEntry* fused_lookup_L2_32(int L1, bool admm);
-const FusedEntry* fused_lookup_L2_64(int L1, bool admm);
-const FusedEntry* fused_lookup_L2_128(int L1, bool admm);
-const FusedEntry* fused_lookup_L2_256(int L1, bool admm);
+const FusedEntry* fused_lookup_L2_16(int L1, bool admm, int tile);
+const FusedEntry* fused_lookup_L2_32(int L1, bool admm, int tile);
+const FusedEntry* fused_lookup_L2_64(int L1, bool admm, int tile);
+const FusedEntry* fused_lookup_L2_128(int L1, bool admm, int tile);
+const FusedEntry* fused_lookup_L2_256(int L1, bool admm, int tile);
 
-const FusedEntry* fused_lookup(int L1, int L2, bool admm) {
+const FusedEntry* fused_lookup(int L1, int L2, bool admm, int tile) {
+  if (tile == 0) tile = kFusedTileElems;
   switch (L2) {
-    case 16: return fused_lookup_L2_16(L1, admm);
-    case 32: return fused_lookup_L2_32(L1, admm);
-    case 64: return fused_lookup_L2_64(L1, admm);
-    case 128: return fused_lookup_L2_128(L1, admm);
-    case 256: return fused_lookup_L2_256(L1, admm);
+    case 16: return fused_lookup_L2_16(L1, admm, tile);
+    case 32: return fused_lookup_L2_32(L1, admm, tile);
+    case 64: return fused_lookup_L2_64(L1, admm, tile);
+    case 128: return fused_lookup_L2_128(L1, admm, tile);
+    case 256: return fused_lookup_L2_256(L1, admm, tile);
     default: return nullptr;
   }
 }

@@ -1,5 +1,7 @@
 // Instantiates the fused solver for one column length L2 = BCCB_L2 and every row
-// length L1 in {16, 32, 64, 128, 256}; the build compiles this file once per L2.
+// length L1 in {16, 32, 64, 128, 256}, with the 8192-element tile and, for grids of
+// at least 8192 elements, the 4096-element tile (twice the CTAs per cluster); the
+// build compiles this file once per L2.
 #include "solver.h"
 
 #ifndef BCCB_L2
@@ -11,16 +13,29 @@
 
 namespace bccb {
 
-const FusedEntry* BCCB_CAT(fused_lookup_L2_, BCCB_L2)(int L1, bool admm) {
+#define BCCB_ENTRIES(L1)                                                            \
+  fused_entry<L1, BCCB_L2, false>(), fused_entry<L1, BCCB_L2, true>()
+#define BCCB_ENTRIES_HALF(L1)                                                       \
+  fused_entry<L1, BCCB_L2, false, 4096>(), fused_entry<L1, BCCB_L2, true, 4096>()
+
+const FusedEntry* BCCB_CAT(fused_lookup_L2_, BCCB_L2)(int L1, bool admm, int tile) {
   static const FusedEntry table[] = {
-      fused_entry<16, BCCB_L2, false>(),  fused_entry<16, BCCB_L2, true>(),
-      fused_entry<32, BCCB_L2, false>(),  fused_entry<32, BCCB_L2, true>(),
-      fused_entry<64, BCCB_L2, false>(),  fused_entry<64, BCCB_L2, true>(),
-      fused_entry<128, BCCB_L2, false>(), fused_entry<128, BCCB_L2, true>(),
-      fused_entry<256, BCCB_L2, false>(), fused_entry<256, BCCB_L2, true>(),
+      BCCB_ENTRIES(16), BCCB_ENTRIES(32), BCCB_ENTRIES(64), BCCB_ENTRIES(128), BCCB_ENTRIES(256),
+#if BCCB_L2 >= 32
+      BCCB_ENTRIES_HALF(256),
+#endif
+#if BCCB_L2 >= 64
+      BCCB_ENTRIES_HALF(128),
+#endif
+#if BCCB_L2 >= 128
+      BCCB_ENTRIES_HALF(64),
+#endif
+#if BCCB_L2 >= 256
+      BCCB_ENTRIES_HALF(32),
+#endif
   };
   for (const FusedEntry& e : table)
-    if (e.L1 == L1 && e.admm == (admm ? 1 : 0)) return &e;
+    if (e.L1 == L1 && e.admm == (admm ? 1 : 0) && e.tile == tile) return &e;
   return nullptr;
 }
 

@@ -12,8 +12,6 @@
 // The subtraction b - G x happens in the Fourier domain, where its operands are of
 // the size of the data residual, and directions the Gram does not see pass through
 // exactly; both keep FP32 round-off from being amplified by FISTA's momentum.
-// q and Bt vanish off the element mask (Lambda = 0), so the middle stage skips
-// those frequencies.
 //
 // Layout.  The grid is stored L2 rows x L1 columns, row-major (the paper's
 // vec(C) with C in C^{L1 x L2}, Section III-B).  A cluster of C CTAs owns one
@@ -21,14 +19,17 @@
 // memory for the whole solve, so the iterations never touch HBM except for the
 // nonzero Fourier-domain multiplier entries, read through L2.
 //
-// Transform.  Row DFTs (length L1) are local.  The column DFT of length L2 is
-// split as L2 = Q * R' (decimation in time): group g = c + C*v (v < Q/C) holds
-// the rows g + Q*t; every CTA runs the R'-point DFTs of its groups locally, then
-// the final radix-Q stage combines one value from each group.  That stage is the
-// only cross-CTA step: each CTA takes a 1/C share of the (frequency k1, column)
-// pairs, gathers its Q operands from the cluster's shared memory (DSMEM), runs
-// the forward radix-Q butterfly, multiplies by m, runs the inverse radix-Q
-// butterfly and scatters the results back.  Two cluster barriers per iteration.
+// Transform.  Row DFTs (length L1) are local; each warp owns whole rows, so the
+// row stages synchronise only the warp.  The column DFT of length L2 is split as
+// L2 = Q * R' (decimation in time): group g = c + C*v (v < Q/C) holds the rows
+// g + Q*t; every CTA runs the R'-point DFTs of its groups locally (one in-place
+// stage), then the final radix-Q stage combines one value from each group.  That
+// stage is the only cross-CTA step: each CTA takes a 1/C share of the (frequency
+// k1, column) pairs, gathers its Q operands from the cluster's shared memory
+// (DSMEM), runs the forward radix-Q butterfly, applies q and Bt, runs the inverse
+// butterfly and scatters the results back.  q and Bt vanish off the element mask
+// (Lambda = 0); a pair whose Q frequencies all vanish stores zeros without any
+// load or butterfly.  Per iteration: two CTA barriers and two cluster barriers.
 // Local DFTs are in-place Stockham stages (radix 16, last stage 2/4/8/16) with
 // the operands staged in registers; shared rows are padded by one element per
 // 16 to keep the strided stage writes free of bank conflicts.
@@ -46,7 +47,7 @@ struct FusedInst {
   int64_t g_off;  // offset of this instance's grids in FusedArgs::mult / ::bt
   int64_t c_off;  // offset of this instance's solution in c_out / aux_out / c0
   float kappa;    // threshold mu*lam (ISTA/FISTA) or lam/rho (ADMM), set by the setup kernels
-  int pad_;
+  int kcols;      // 1 + the largest Fourier column p1 where q or Bt is nonzero (set by setup)
 };
 
 struct FusedArgs {
@@ -66,29 +67,36 @@ struct FusedArgs {
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 __host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
 
-// Elements of the grid held by one CTA: at most 8192 (64 KB of complex64).
+// Elements of the grid held by one CTA: at most 8192 (64 KB of complex64); the
+// 4096-element tile doubles the cluster and fits two CTAs per SM.
 constexpr int kFusedTileElems = 8192;
 
-template <int L1_, int L2_, bool ADMM_>
+template <int L1_, int L2_, bool ADMM_, int TILE_ = kFusedTileElems>
 struct FusedShape {
-  static constexpr int L1 = L1_, L2 = L2_;
+  static constexpr int L1 = L1_, L2 = L2_, TILE = TILE_;
   static constexpr bool ADMM = ADMM_;
-  static constexpr int C = cmax(1, (L1 * L2) / kFusedTileElems);  // CTAs per cluster
+  static constexpr int C = cmax(1, (L1 * L2) / TILE);  // CTAs per cluster
   static constexpr int R = L2 / C;                                // rows per CTA
   static constexpr int E = R * L1;                                // elements per CTA
   static constexpr int T = cmax(32, E / 16);                      // threads per CTA
+  static constexpr int V = E / T;                                 // elements per thread per stage
   static constexpr int Q = cmin(16, L2);                          // cross-group radix
   static constexpr int QV = Q / C;                                // groups per CTA
   static constexpr int RP = L2 / Q;                               // local column DFT length
   static constexpr int P = L1 + L1 / 16;                          // padded row pitch
   static constexpr int NMAX = cmax(L1, L2);
   static constexpr int SH = RP * L1 / C;                          // middle-stage pairs per CTA
-  // work (padded) + two state grids + a flag byte per owned frequency + twiddles
-  static constexpr int SMEM = (R * P + 2 * E) * 8 + E + NMAX * 8;
+  // each warp owns 512/L1 whole rows through every row stage
+  static constexpr bool ROW_WARP = (V == 16) && (L1 <= 512) && ((32 * V) % L1 == 0);
+  // work (padded) + two state grids + twiddles + a frequency bit mask per middle-stage pair
+  static constexpr int SMEM = (R * P + 2 * E) * 8 + NMAX * 8 + SH * 2;
+  // two CTAs per SM when their shared memory fits (227 KB per CTA, 228 KB per SM)
+  static constexpr int MIN_BLOCKS = (2 * (SMEM + 1024) <= 228 * 1024) ? 2 : 1;
   static_assert(L1 >= 16 && L2 >= 16, "fused path needs L1, L2 >= 16");
-  static_assert(C <= 8, "cluster larger than 8 CTAs");
+  static_assert(C <= 16, "cluster larger than 16 CTAs");
   static_assert(QV * C == Q, "cluster size must divide the cross-group radix");
   static_assert(SH * C == RP * L1, "middle-stage pairs must split evenly");
+  static_assert(num_stages(RP) <= 1, "local column DFT is a single stage");
   static_assert(E % 16 == 0, "tile");
 };
 
@@ -104,44 +112,76 @@ __device__ __forceinline__ float2 soft_threshold(float2 u, float kappa) {
   return make_float2(0.0f, 0.0f);
 }
 
+// ---- distributed shared memory with 32-bit shared::cluster addresses
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint32_t cluster_map(uint32_t a, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ float2 ld_cluster(uint32_t a) {
+  float2 v;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_cluster(uint32_t a, float2 v) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
+}
+
+// read-only global loads kept in program order (the compiler may not hoist them)
+__device__ __forceinline__ float ld_ro_f32(const float* p) {
+  float v;
+  asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float2 ld_ro_f32x2(const float2* p) {
+  float2 v;
+  asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+  return v;
+}
+
 template <typename S>
 struct FusedCta {
   static constexpr int L1 = S::L1, L2 = S::L2, C = S::C, R = S::R, E = S::E, T = S::T;
   static constexpr int Q = S::Q, QV = S::QV, RP = S::RP, P = S::P, NMAX = S::NMAX, SH = S::SH;
 
-  float2* work;        // R x P (padded)
-  float2* s0;          // E: c (ISTA/FISTA) or z (ADMM)
-  float2* s1;          // E: z (FISTA) or v (ADMM)
-  uint8_t* flag;       // E: 1 where this CTA's middle-stage frequency has q != 0
-  float2* tw;          // NMAX twiddles W_NMAX^e
+  float2* work;     // R x P (padded)
+  float2* s0;       // E: c (ISTA/FISTA) or z (ADMM)
+  float2* s1;       // E: z (FISTA) or v (ADMM)
+  float2* tw;       // NMAX twiddles W_NMAX^e
+  uint16_t* pmask;  // SH: bit q set when frequency (k1 + RP q, col) of pair pl has q != 0
   int crank;
   int tid;
 
   // ---------------------------------------------------------------------------------------
-  // one in-place Stockham stage over all R rows (length L1), radix RS, stride NS
-  // EPI: instead of storing, hand each output (row, column, value) to the epilogue
+  // one in-place Stockham stage over all R rows (length L1), radix RS, stride NS; the
+  // epilogue functor receives every output (row, column, value)
   // ---------------------------------------------------------------------------------------
+  // kin: columns >= kin hold zeros and are not loaded (the first inverse stage after
+  // the middle stage, whose spectrum vanishes beyond the instance's active columns)
   template <int RS, int NS, bool INV, typename Epi>
-  __device__ __forceinline__ void row_stage(Epi&& epi) {
+  __device__ __forceinline__ void row_stage(Epi&& epi, int kin = L1) {
     constexpr int NBR = L1 / RS;
-    constexpr int NB = R * NBR;
-    constexpr int NBT = (NB + T - 1) / T;
-    float2 v[NBT][RS];
+    if constexpr (S::ROW_WARP) {
+      constexpr int RPW = 512 / L1;          // rows per warp
+      constexpr int NBT = (RPW * NBR) / 32;  // butterflies per thread (= 16 / RS)
+      const int warp = tid >> 5, lane = tid & 31;
+      float2 v[NBT][RS];
 #pragma unroll
-    for (int k = 0; k < NBT; ++k) {
-      const int b = tid + k * T;
-      if (NB % T == 0 || b < NB) {
-        const int row = b / NBR, j = b % NBR;
+      for (int k = 0; k < NBT; ++k) {
+        const int bw = lane + 32 * k;
+        const int row = warp * RPW + bw / NBR, j = bw % NBR;
 #pragma unroll
-        for (int i = 0; i < RS; ++i) v[k][i] = work[row * P + pad16(j + i * NBR)];
+        for (int i = 0; i < RS; ++i)
+          v[k][i] = (j + i * NBR < kin) ? work[row * P + pad16(j + i * NBR)] : make_float2(0.f, 0.f);
       }
-    }
-    __syncthreads();
+      __syncwarp();
 #pragma unroll
-    for (int k = 0; k < NBT; ++k) {
-      const int b = tid + k * T;
-      if (NB % T == 0 || b < NB) {
-        const int row = b / NBR, j = b % NBR;
+      for (int k = 0; k < NBT; ++k) {
+        const int bw = lane + 32 * k;
+        const int row = warp * RPW + bw / NBR, j = bw % NBR;
         const int kk = j % NS;
         if constexpr (NS > 1) {
 #pragma unroll
@@ -152,119 +192,182 @@ struct FusedCta {
 #pragma unroll
         for (int i = 0; i < RS; ++i) epi(row, base + i * NS, v[k][i]);
       }
+      __syncwarp();
+    } else {
+      constexpr int NB = R * NBR;
+      constexpr int NBT = (NB + T - 1) / T;
+      float2 v[NBT][RS];
+#pragma unroll
+      for (int k = 0; k < NBT; ++k) {
+        const int b = tid + k * T;
+        if (NB % T == 0 || b < NB) {
+          const int row = b / NBR, j = b % NBR;
+#pragma unroll
+          for (int i = 0; i < RS; ++i)
+            v[k][i] = (j + i * NBR < kin) ? work[row * P + pad16(j + i * NBR)] : make_float2(0.f, 0.f);
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < NBT; ++k) {
+        const int b = tid + k * T;
+        if (NB % T == 0 || b < NB) {
+          const int row = b / NBR, j = b % NBR;
+          const int kk = j % NS;
+          if constexpr (NS > 1) {
+#pragma unroll
+            for (int i = 1; i < RS; ++i) v[k][i] = twmul<INV>(v[k][i], tw[i * kk * (NMAX / (NS * RS))]);
+          }
+          Dft<RS, INV, float2>::run(v[k]);
+          const int base = (j / NS) * NS * RS + kk;
+#pragma unroll
+          for (int i = 0; i < RS; ++i) epi(row, base + i * NS, v[k][i]);
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
 
   template <int STG, bool INV, typename Epi>
-  __device__ __forceinline__ void row_fft_from(Epi&& last_epi) {
+  __device__ __forceinline__ void row_fft_from(Epi&& last_epi, int kin) {
     constexpr int NST = num_stages(L1);
     constexpr int RS = radix_of(L1, STG);
     constexpr int NS = 1 << (4 * STG);
+    const int k = (STG == 0) ? kin : L1;
     if constexpr (STG == NST - 1) {
-      row_stage<RS, NS, INV>(last_epi);
+      row_stage<RS, NS, INV>(last_epi, k);
     } else {
-      row_stage<RS, NS, INV>([&](int row, int e, float2 x) { work[row * P + pad16(e)] = x; });
-      row_fft_from<STG + 1, INV>(last_epi);
+      row_stage<RS, NS, INV>([&](int row, int e, float2 x) { work[row * P + pad16(e)] = x; }, k);
+      row_fft_from<STG + 1, INV>(last_epi, kin);
     }
   }
 
   // ---------------------------------------------------------------------------------------
-  // local column DFTs: QV groups x L1 columns, length RP; group v holds local rows v + QV*t
+  // local column DFTs: QV groups x L1 columns, length RP, a single radix-RP stage;
+  // group g holds local rows g + QV*t.  Each thread reads and writes the same RP
+  // positions, so the stage needs no barrier of its own.
   // ---------------------------------------------------------------------------------------
-  template <int RS, int NS, bool INV>
-  __device__ __forceinline__ void col_stage() {
-    constexpr int NBS = RP / RS;
-    constexpr int NB = QV * L1 * NBS;
-    constexpr int NBT = (NB + T - 1) / T;
-    float2 v[NBT][RS];
+  template <bool INV>
+  __device__ __forceinline__ void col_dft(int kc) {
+    if constexpr (RP > 1) {
+      constexpr int NB = QV * L1;
+      constexpr int NBT = (NB + T - 1) / T;
 #pragma unroll
-    for (int k = 0; k < NBT; ++k) {
-      const int b = tid + k * T;
-      if (NB % T == 0 || b < NB) {
-        const int col = b % L1, rest = b / L1, g = rest % QV, j = rest / QV;
+      for (int k = 0; k < NBT; ++k) {
+        const int b = tid + k * T;
+        if ((NB % T == 0 || b < NB) && (b % L1) < kc) {
+          const int col = b % L1, g = b / L1;
+          float2 v[RP];
 #pragma unroll
-        for (int i = 0; i < RS; ++i) v[k][i] = work[(g + QV * (j + i * NBS)) * P + pad16(col)];
-      }
-    }
-    __syncthreads();
+          for (int i = 0; i < RP; ++i) v[i] = work[(g + QV * i) * P + pad16(col)];
+          Dft<RP, INV, float2>::run(v);
 #pragma unroll
-    for (int k = 0; k < NBT; ++k) {
-      const int b = tid + k * T;
-      if (NB % T == 0 || b < NB) {
-        const int col = b % L1, rest = b / L1, g = rest % QV, j = rest / QV;
-        const int kk = j % NS;
-        if constexpr (NS > 1) {
-#pragma unroll
-          for (int i = 1; i < RS; ++i) v[k][i] = twmul<INV>(v[k][i], tw[i * kk * (NMAX / (NS * RS))]);
+          for (int i = 0; i < RP; ++i) work[(g + QV * i) * P + pad16(col)] = v[i];
         }
-        Dft<RS, INV, float2>::run(v[k]);
-        const int base = (j / NS) * NS * RS + kk;
-#pragma unroll
-        for (int i = 0; i < RS; ++i) work[(g + QV * (base + i * NS)) * P + pad16(col)] = v[k][i];
       }
     }
-    __syncthreads();
-  }
-
-  template <int STG, bool INV>
-  __device__ __forceinline__ void col_fft_from() {
-    constexpr int NST = num_stages(RP);
-    if constexpr (STG < NST) {
-      col_stage<radix_of(RP, STG), (1 << (4 * STG)), INV>();
-      col_fft_from<STG + 1, INV>();
-    }
   }
 
   // ---------------------------------------------------------------------------------------
-  // cross-group radix-Q stage, Fourier multiplier, inverse radix-Q stage (in place)
+  // cross-group radix-Q stage, Fourier-domain update, inverse radix-Q stage (in place)
   // ---------------------------------------------------------------------------------------
-  __device__ __forceinline__ void middle(float2* const* peer, const float* mult_g, const float2* bt_g) {
+  __device__ __forceinline__ void middle(const uint32_t* peer, const float* mult_g, const float2* bt_g, int kc) {
     constexpr int PT = (SH + T - 1) / T;
 #pragma unroll
     for (int k = 0; k < PT; ++k) {
       const int pl = tid + k * T;
-      if (SH % T == 0 || pl < SH) {
+      if ((SH % T == 0 || pl < SH) && ((crank * SH + pl) % L1) < kc) {
         const int p = crank * SH + pl;
         const int k1 = p / L1, col = p % L1;
+        const uint32_t pm = pmask[pl];
         float2 v[Q];
-#pragma unroll
-        for (int g = 0; g < Q; ++g) {
-          const int c = g % C, vv = g / C;
-          v[g] = peer[c][(vv + QV * k1) * P + pad16(col)];
-        }
-#pragma unroll
-        for (int g = 1; g < Q; ++g) v[g] = twmul<false>(v[g], tw[g * k1 * (NMAX / L2)]);
-        Dft<Q, false, float2>::run(v);
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-          if (flag[q * SH + pl]) {
-            const int f = (k1 + RP * q) * L1 + col;
-            const float m = __ldg(&mult_g[f]);
-            const float2 b = __ldg(&bt_g[f]);
-            v[q] = make_float2(v[q].x * m - b.x, v[q].y * m - b.y);
-          } else {
-            v[q] = make_float2(0.f, 0.f);
+        if (pm != 0) {
+          // The first two nonzero frequencies of the pair (the common case off a
+          // sparse mask) are fetched now, so their latency hides behind the gather
+          // and the forward butterfly; any further ones are read when needed.
+          const int q0 = __ffs(pm) - 1;
+          const uint32_t rest = pm & (pm - 1);
+          const int q1 = rest ? __ffs(rest) - 1 : -1;
+          const int f0 = (k1 + RP * q0) * L1 + col;
+          const float m0 = ld_ro_f32(&mult_g[f0]);
+          const float2 b0 = ld_ro_f32x2(&bt_g[f0]);
+          float m1 = 0.f;
+          float2 b1 = make_float2(0.f, 0.f);
+          if (q1 >= 0) {
+            const int f1 = (k1 + RP * q1) * L1 + col;
+            m1 = ld_ro_f32(&mult_g[f1]);
+            b1 = ld_ro_f32x2(&bt_g[f1]);
           }
-        }
-        Dft<Q, true, float2>::run(v);
 #pragma unroll
-        for (int g = 1; g < Q; ++g) v[g] = twmul<true>(v[g], tw[g * k1 * (NMAX / L2)]);
+          for (int g = 0; g < Q; ++g) {
+            const int c = g % C, vv = g / C;
+            const int off = (vv + QV * k1) * P + pad16(col);
+            if constexpr (C > 1) {
+              v[g] = ld_cluster(peer[c] + off * 8);
+            } else {
+              v[g] = work[off];
+            }
+          }
+#pragma unroll
+          for (int g = 1; g < Q; ++g) v[g] = twmul<false>(v[g], tw[g * k1 * (NMAX / L2)]);
+          Dft<Q, false, float2>::run(v);
+#pragma unroll
+          for (int q = 0; q < Q; ++q) {
+            if (pm & (1u << q)) {
+              float m;
+              float2 b;
+              if (q == q0) {
+                m = m0;
+                b = b0;
+              } else if (q == q1) {
+                m = m1;
+                b = b1;
+              } else {
+                const int f = (k1 + RP * q) * L1 + col;
+                m = ld_ro_f32(&mult_g[f]);
+                b = ld_ro_f32x2(&bt_g[f]);
+              }
+              v[q] = make_float2(v[q].x * m - b.x, v[q].y * m - b.y);
+            } else {
+              v[q] = make_float2(0.f, 0.f);
+            }
+          }
+          Dft<Q, true, float2>::run(v);
+#pragma unroll
+          for (int g = 1; g < Q; ++g) v[g] = twmul<true>(v[g], tw[g * k1 * (NMAX / L2)]);
+        } else {
+#pragma unroll
+          for (int g = 0; g < Q; ++g) v[g] = make_float2(0.f, 0.f);
+        }
 #pragma unroll
         for (int g = 0; g < Q; ++g) {
           const int c = g % C, vv = g / C;
-          peer[c][(vv + QV * k1) * P + pad16(col)] = v[g];
+          const int off = (vv + QV * k1) * P + pad16(col);
+          if constexpr (C > 1) {
+            st_cluster(peer[c] + off * 8, v[g]);
+          } else {
+            work[off] = v[g];
+          }
         }
       }
     }
   }
 };
 
-template <int L1, int L2, bool ADMM>
-__global__ void __launch_bounds__(FusedShape<L1, L2, ADMM>::T, 1)
+template <int C>
+__device__ __forceinline__ void cluster_barrier() {
+  if constexpr (C > 1) {
+    cg::this_cluster().sync();
+  } else {
+    __syncthreads();
+  }
+}
+
+template <int L1, int L2, bool ADMM, int TILE>
+__global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<L1, L2, ADMM, TILE>::MIN_BLOCKS)
     fused_solve_kernel(const FusedArgs a) {
-  using S = FusedShape<L1, L2, ADMM>;
-  constexpr int C = S::C, R = S::R, E = S::E, T = S::T, P = S::P, NMAX = S::NMAX;
+  using S = FusedShape<L1, L2, ADMM, TILE>;
+  constexpr int C = S::C, E = S::E, T = S::T, P = S::P, NMAX = S::NMAX, R = S::R;
   constexpr int Q = S::Q, RP = S::RP, SH = S::SH;
 
   extern __shared__ float4 smem_raw[];
@@ -278,7 +381,7 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM>::T, 1)
   sp += E * 8;
   cta.tw = reinterpret_cast<float2*>(sp);
   sp += NMAX * 8;
-  cta.flag = reinterpret_cast<uint8_t*>(sp);
+  cta.pmask = reinterpret_cast<uint16_t*>(sp);
   cta.tid = threadIdx.x;
   int crank = 0;
   if constexpr (C > 1) crank = (int)cg::this_cluster().block_rank();
@@ -287,36 +390,40 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM>::T, 1)
   const int inst_id = a.ids[blockIdx.x / C];
   const FusedInst in = a.insts[inst_id];
   const float kappa = in.kappa;
+  // active Fourier columns, rounded up to a multiple of 16 (every column when the
+  // instance's multiplier reaches past that)
+  const int kc = min(L1, (in.kcols + 15) & ~15);
   const float* mult = a.mult + in.g_off;
   const float2* bt = a.bt + in.g_off;
   const float2* c0 = a.c0 ? a.c0 + in.c_off : nullptr;
   float2* c_out = a.c_out + in.c_off;
   float2* aux_out = a.aux_out ? a.aux_out + in.c_off : nullptr;
 
-  float2* peer[C];
-  if constexpr (C > 1) {
-    cg::cluster_group cl = cg::this_cluster();
+  uint32_t peer[C];
+  {
+    const uint32_t w = smem_addr(cta.work);
 #pragma unroll
-    for (int c = 0; c < C; ++c) peer[c] = cl.map_shared_rank(cta.work, c);
-  } else {
-    peer[0] = cta.work;
+    for (int c = 0; c < C; ++c) peer[c] = (C > 1) ? cluster_map(w, c) : w;
   }
 
-  // ---- load twiddles, multiplier share, initial state
+  // ---- load twiddles, the frequency masks and the initial state
   for (int e = threadIdx.x; e < NMAX; e += T) cta.tw[e] = a.twiddle[e * (kTwiddleLen / NMAX)];
-  for (int idx = threadIdx.x; idx < E; idx += T) {
-    const int q = idx / SH, pl = idx % SH;
+  for (int pl = threadIdx.x; pl < SH; pl += T) {
     const int p = crank * SH + pl;
     const int k1 = p / L1, col = p % L1;
-    const int f = (k1 + RP * q) * L1 + col;
-    cta.flag[idx] = (mult[f] != 0.f || bt[f].x != 0.f || bt[f].y != 0.f) ? 1 : 0;
+    uint32_t pm = 0;
+    for (int q = 0; q < Q; ++q) {
+      const int f = (k1 + RP * q) * L1 + col;
+      if (mult[f] != 0.f || bt[f].x != 0.f || bt[f].y != 0.f) pm |= 1u << q;
+    }
+    cta.pmask[pl] = (uint16_t)pm;
   }
   for (int idx = threadIdx.x; idx < E; idx += T) {
     const int s = idx / L1, e = idx % L1;
     const int gidx = (crank + C * s) * L1 + e;
     float2 x = c0 ? c0[gidx] : make_float2(0.f, 0.f);
-    cta.s0[idx] = x;                                        // c^(0) or z^(0)
-    cta.s1[idx] = ADMM ? make_float2(0.f, 0.f) : x;         // z^(1) = c^(0), or v^(0) = 0
+    cta.s0[idx] = x;                                 // c^(0) or z^(0)
+    cta.s1[idx] = ADMM ? make_float2(0.f, 0.f) : x;  // z^(1) = c^(0), or v^(0) = 0
     cta.work[s * P + pad16(e)] = x;
   }
   __syncthreads();
@@ -326,16 +433,18 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM>::T, 1)
     const float beta = fista ? __ldg(&a.beta[it]) : 0.0f;
     const bool last = (it == a.iters - 1);
 
-    // forward row DFTs (store in place)
     cta.template row_fft_from<0, false>(
-        [&](int row, int e, float2 x) { cta.work[row * P + pad16(e)] = x; });
-    // forward local column DFTs
-    cta.template col_fft_from<0, false>();
-    if constexpr (C > 1) cg::this_cluster().sync(); else __syncthreads();
-    cta.middle(peer, mult, bt);
-    if constexpr (C > 1) cg::this_cluster().sync(); else __syncthreads();
-    cta.template col_fft_from<0, true>();
-    // inverse row DFTs with the fused epilogue
+        [&](int row, int e, float2 x) {
+          if (e < kc) cta.work[row * P + pad16(e)] = x;
+        },
+        L1);
+    __syncthreads();
+    cta.template col_dft<false>(kc);
+    cluster_barrier<C>();
+    cta.middle(peer, mult, bt, kc);
+    cluster_barrier<C>();
+    cta.template col_dft<true>(kc);
+    __syncthreads();
     cta.template row_fft_from<0, true>([&](int row, int e, float2 g) {
       const int sidx = row * L1 + e;
       if constexpr (!ADMM) {
@@ -362,14 +471,16 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM>::T, 1)
         cta.work[row * P + pad16(e)] = make_float2(zn.x - vn.x, zn.y - vn.y);
         if (last && aux_out) aux_out[(crank + C * row) * L1 + e] = make_float2(un.x - vo.x, un.y - vo.y);
       }
-    });
+    }, kc);
   }
 
   // ---- write the result
+  __syncthreads();
   for (int idx = threadIdx.x; idx < E; idx += T) {
     const int s = idx / L1, e = idx % L1;
     c_out[(crank + C * s) * L1 + e] = cta.s0[idx];
   }
+  // no CTA may leave while a peer can still address its shared memory
   if constexpr (C > 1) cg::this_cluster().sync();
 }
 
@@ -377,22 +488,26 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM>::T, 1)
 // host-side launch table
 // ------------------------------------------------------------------------------------------
 struct FusedEntry {
-  int L1, L2, admm;
+  int L1, L2, admm, tile;
   int cluster, threads, smem;
   cudaError_t (*launch)(const FusedArgs&, int n_inst, cudaStream_t);
   cudaError_t (*prepare)();
 };
 
-template <int L1, int L2, bool ADMM>
+template <int L1, int L2, bool ADMM, int TILE>
 cudaError_t fused_prepare() {
-  using S = FusedShape<L1, L2, ADMM>;
-  return cudaFuncSetAttribute(fused_solve_kernel<L1, L2, ADMM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              S::SMEM);
+  using S = FusedShape<L1, L2, ADMM, TILE>;
+  cudaError_t e = cudaFuncSetAttribute(fused_solve_kernel<L1, L2, ADMM, TILE>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+  if (e == cudaSuccess && S::C > 8)
+    e = cudaFuncSetAttribute(fused_solve_kernel<L1, L2, ADMM, TILE>, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                             1);
+  return e;
 }
 
-template <int L1, int L2, bool ADMM>
+template <int L1, int L2, bool ADMM, int TILE>
 cudaError_t fused_launch(const FusedArgs& a, int n_inst, cudaStream_t st) {
-  using S = FusedShape<L1, L2, ADMM>;
+  using S = FusedShape<L1, L2, ADMM, TILE>;
   if (n_inst <= 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(n_inst * S::C), 1, 1);
@@ -406,14 +521,14 @@ cudaError_t fused_launch(const FusedArgs& a, int n_inst, cudaStream_t st) {
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, fused_solve_kernel<L1, L2, ADMM>, a);
+  return cudaLaunchKernelEx(&cfg, fused_solve_kernel<L1, L2, ADMM, TILE>, a);
 }
 
-template <int L1, int L2, bool ADMM>
+template <int L1, int L2, bool ADMM, int TILE = kFusedTileElems>
 FusedEntry fused_entry() {
-  using S = FusedShape<L1, L2, ADMM>;
-  return FusedEntry{L1, L2, ADMM ? 1 : 0, S::C, S::T, S::SMEM, &fused_launch<L1, L2, ADMM>,
-                    &fused_prepare<L1, L2, ADMM>};
+  using S = FusedShape<L1, L2, ADMM, TILE>;
+  return FusedEntry{L1, L2, ADMM ? 1 : 0, TILE, S::C, S::T, S::SMEM, &fused_launch<L1, L2, ADMM, TILE>,
+                    &fused_prepare<L1, L2, ADMM, TILE>};
 }
 
 }  // namespace bccb

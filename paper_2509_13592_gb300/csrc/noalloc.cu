@@ -81,7 +81,7 @@ __global__ void records_kernel(bccb::InstDesc d, bccb::InstDesc* desc, bccb::Fus
   f.g_off = 0;
   f.c_off = 0;
   f.kappa = 0.f;
-  f.pad_ = 0;
+  f.kcols = d.L1;
   fused[0] = f;
   ids[0] = 0;
 }

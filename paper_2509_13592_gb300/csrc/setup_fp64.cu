@@ -150,7 +150,7 @@ struct SumOp {
 // round-off of the FP64 DFTs of an exactly zero eigenvalue and are set to 0.
 __global__ void eig_mult_kernel(const InstDesc* __restrict__ desc, const double2* __restrict__ lam_c,
                                 const double2* __restrict__ sgrid, double* lam64, InstParams* par, float* mult,
-                                float2* bt, int algo, double rho) {
+                                float2* bt, FusedInst* fused, int algo, double rho) {
   __shared__ double sh[32];
   const InstDesc d = desc[blockIdx.x];
   const int L = d.L1 * d.L2;
@@ -159,6 +159,7 @@ __global__ void eig_mult_kernel(const InstDesc* __restrict__ desc, const double2
   top = block_reduce(top, MaxOp(), sh, 0.0);
   const double mu = 1.0 / top;
   const double inv_L = 1.0 / (double)L;
+  double kc = 0.0;  // 1 + largest Fourier column with a nonzero multiplier or constant term
   for (int cell = threadIdx.x; cell < L; cell += blockDim.x) {
     double lv = lam_c[d.g_off + cell].x;
     if (lv < 1e-9 * top) lv = 0.0;
@@ -172,12 +173,17 @@ __global__ void eig_mult_kernel(const InstDesc* __restrict__ desc, const double2
       m = mu * lv * inv_L;
       bs = mu;
     }
-    mult[d.g_off + cell] = (float)m;
-    bt[d.g_off + cell] = make_float2((float)(sv.x * bs), (float)(sv.y * bs));
+    const float mf = (float)m;
+    const float2 bf = make_float2((float)(sv.x * bs), (float)(sv.y * bs));
+    mult[d.g_off + cell] = mf;
+    bt[d.g_off + cell] = bf;
+    if (mf != 0.f || bf.x != 0.f || bf.y != 0.f) kc = fmax(kc, (double)(cell % d.L1 + 1));
   }
+  kc = block_reduce(kc, MaxOp(), sh, 0.0);
   if (threadIdx.x == 0) {
     par[blockIdx.x].mu = mu;
     par[blockIdx.x].lam_top = top;
+    fused[blockIdx.x].kcols = (int)kc;
   }
 }
 
@@ -353,7 +359,7 @@ cudaError_t run_setup(bccb_solver* s, const float2* y_dev) {
   if ((err = fft2_64(s, s->d_w64, 1)) != cudaSuccess) return err;  // first column of the Gram
   if ((err = fft2_64(s, s->d_w64, 0)) != cudaSuccess) return err;  // Lambda (eq:lambda)
   eig_mult_kernel<<<s->n, kThreads, 0, s->stream>>>(s->d_desc, s->d_w64, s->d_b64, s->d_lam64, s->d_par,
-                                                     s->d_mult, s->d_cterm, s->algo, s->rho);
+                                                     s->d_mult, s->d_cterm, s->d_fused, s->algo, s->rho);
   if ((err = fft2_64(s, s->d_b64, 1)) != cudaSuccess) return err;  // b = A^H y
   lam_kappa_kernel<<<s->n, kThreads, 0, s->stream>>>(s->d_desc, s->d_b64, s->d_par, s->d_fused, s->algo, s->rho);
   return cudaGetLastError();

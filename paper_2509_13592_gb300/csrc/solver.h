@@ -80,6 +80,14 @@ struct bccb_solver {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   int64_t launches = 0;  // kernels launched by the last solve
   bool last_checked = false;
+  // per-class streams forked from `stream` (classes run concurrently)
+  std::vector<cudaStream_t> class_streams;
+  std::vector<cudaEvent_t> class_done;
+  cudaEvent_t fork = nullptr;
+  // captured solve (bccb_batch_capture / bccb_batch_replay)
+  cudaGraphExec_t graph = nullptr;
+  // probe output for the autotuner
+  float2* d_probe = nullptr;
 };
 
 namespace bccb {
@@ -91,6 +99,6 @@ cudaError_t fill_twiddles(bccb_solver* s);
 cudaError_t fista_schedule(bccb_solver* s, int iters);
 // shared-memory opt-in of the FP64 column pass for grids with up to max_L2 rows
 cudaError_t prepare_fp64_passes(int max_L2);
-// fused_L*.cu
-const FusedEntry* fused_lookup(int L1, int L2, bool admm);
+// fused_inst.cu / fused_dispatch.cu: tile 0 = the default 8192-element tile
+const FusedEntry* fused_lookup(int L1, int L2, bool admm, int tile = 0);
 }  // namespace bccb

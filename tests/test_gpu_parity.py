@@ -127,6 +127,80 @@ def test_ragged_batch_matches_oracle(lib):
 
 
 # ------------------------------------------------------------------------------------------
+# autotuned tiles and CUDA-graph replay
+# ------------------------------------------------------------------------------------------
+
+
+def _gpu_name():
+    import torch
+
+    return torch.cuda.get_device_name().replace(" ", "_")
+
+
+@pytest.mark.parametrize("algo", ["fista", "admm"])
+def test_both_tiles_match_oracle(lib, algo, tmp_path):
+    """Every tile the autotuner may pick (8192 or 4096 grid elements per CTA) gives the
+    oracle's iterates; the tile is forced through the tuner's cache file."""
+    import torch
+
+    snaps = [synth.config_snapshot(2, 3), synth.make_snapshot(91, 16, 32, 128, 64, 128, 3, 15.0),
+             synth.make_snapshot(92, 32, 16, 128, 256, 64, 3, 15.0)]
+    refs = [oracle_run(s, algo, 120, rho=8.0) for s in snaps]
+    for tile in (8192, 4096):
+        cache = tmp_path / f"tiles_{tile}.txt"
+        cache.write_text("".join(f"{_gpu_name()} {s.L1} {s.L2} {int(algo == 'admm')} {tile}\n" for s in snaps))
+        solver = lib.BatchSolver([inst(s, r["lam"]) for s, r in zip(snaps, refs)], algo, 8.0)
+        y = torch.from_numpy(solver.y_host).cuda()
+        lib.bccb_batch_tune(solver.handle, y, 5, str(cache))
+        for s in snaps:
+            assert lib.bccb_batch_tile(solver.handle, s.L1, s.L2) == tile
+        c = torch.zeros(solver.total_c, dtype=torch.complex64, device="cuda")
+        solver.solve(y, 120, c, check=False)
+        for i, (g, r) in enumerate(zip(solver.unpack(c.cpu().numpy()), refs)):
+            assert_parity(g.reshape(-1), r, what=f"{algo} tile {tile} instance {i}")
+
+
+def test_tuner_measures_and_caches(lib, tmp_path):
+    import torch
+
+    snaps = synth.config_batch(3, 12, first=40)
+    solver = lib.BatchSolver([inst(s, 0.1, lam_is_frac=True) for s in snaps], "fista")
+    y = torch.from_numpy(solver.y_host).cuda()
+    cache = tmp_path / "tiles.txt"
+    lib.bccb_batch_tune(solver.handle, y, 10, str(cache))
+    lines = cache.read_text().split("\n")
+    shapes = {(s.L1, s.L2) for s in snaps}
+    assert len([ln for ln in lines if ln.strip()]) == len(shapes)
+    for (L1, L2) in shapes:
+        assert lib.bccb_batch_tile(solver.handle, L1, L2) in (8192, 4096)
+
+
+def test_graph_replay_matches_direct_solve(lib):
+    import torch
+
+    snaps = synth.config_batch(3, 9, first=60)
+    solver = lib.BatchSolver([inst(s, 0.1, lam_is_frac=True) for s in snaps], "fista",
+                             stream=torch.cuda.Stream())
+    y = torch.from_numpy(solver.y_host).cuda()
+    direct = torch.zeros(solver.total_c, dtype=torch.complex64, device="cuda")
+    replay = torch.full_like(direct, 3.0)
+    torch.cuda.synchronize()  # the solver runs on its own stream
+    solver.solve(y, 150, direct, check=True)
+    res_direct = solver.results()
+    lib.bccb_batch_capture(solver.handle, y, 150, None, replay, None, True)
+    for _ in range(2):
+        lib.bccb_batch_replay(solver.handle)
+        res = solver.results()  # synchronises the solver's stream
+        assert torch.equal(replay, direct)
+        np.testing.assert_array_equal(res["kkt"], res_direct["kkt"])
+        replay.fill_(5.0)
+        torch.cuda.synchronize()
+    lib.bccb_batch_replay(solver.handle)
+    solver.results()
+    assert torch.equal(replay, direct)
+
+
+# ------------------------------------------------------------------------------------------
 # edge cases
 # ------------------------------------------------------------------------------------------
 
