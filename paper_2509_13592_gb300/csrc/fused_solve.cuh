@@ -88,6 +88,9 @@ struct FusedShape {
   static constexpr int SH = RP * L1 / C;                          // middle-stage pairs per CTA
   // each warp owns 512/L1 whole rows through every row stage
   static constexpr bool ROW_WARP = (V == 16) && (L1 <= 512) && ((32 * V) % L1 == 0);
+  // rows of 256 = 16 x 16: a thread reads and writes the same 16 positions in the
+  // last inverse and the first forward row stage (see FusedCta::sq_*)
+  static constexpr bool SQ16 = ROW_WARP && (L1 == 256);
   // work (padded) + two state grids + twiddles + a frequency bit mask per middle-stage pair
   static constexpr int SMEM = (R * P + 2 * E) * 8 + NMAX * 8 + SH * 2;
   // two CTAs per SM when their shared memory fits (227 KB per CTA, 228 KB per SM)
@@ -269,6 +272,112 @@ struct FusedCta {
   }
 
   // ---------------------------------------------------------------------------------------
+  // Rows of 256 = 16 x 16 (two radix-16 Stockham stages).  Thread (row, j), j < 16,
+  // reads positions j + 16 i in both stages and writes 16 j + k in the first, j + 16 k
+  // in the second.  Only the first nz = kc/16 Fourier column blocks are nonzero
+  // after the middle stage and only they are needed after the forward transform, so
+  // the forward second stage forms just its first nz outputs and the inverse first
+  // stage reads just its first nz inputs.
+  // ---------------------------------------------------------------------------------------
+  __device__ __forceinline__ void sq_rowj(int& row, int& j) const {
+    row = (tid >> 5) * 2 + ((tid & 31) >> 4);
+    j = tid & 15;
+  }
+
+  // forward first stage from the work rows (used once, before the first iteration)
+  __device__ __forceinline__ void sq_fwd1_from_work() {
+    int row, j;
+    sq_rowj(row, j);
+    float2 v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = work[row * P + pad16(j + 16 * i)];
+    __syncwarp();
+    Dft<16, false, float2>::run(v);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) work[row * P + pad16(16 * j + k)] = v[k];
+    __syncwarp();
+  }
+
+  // forward second stage, outputs j + 16 k2 for k2 < nz only
+  __device__ __forceinline__ void sq_fwd2(int nz) {
+    int row, j;
+    sq_rowj(row, j);
+    float2 v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = work[row * P + pad16(j + 16 * i)];
+    __syncwarp();
+#pragma unroll
+    for (int i = 1; i < 16; ++i) v[i] = twmul<false>(v[i], tw[i * j * (NMAX / 256)]);
+    if (nz == 1) {
+      float2 s0 = v[0];
+#pragma unroll
+      for (int i = 1; i < 16; ++i) s0 = cadd(s0, v[i]);
+      work[row * P + pad16(j)] = s0;
+    } else if (nz == 2) {
+      // outputs k2 = 0 and 1 of the 16-point DFT: sum_i v_i and sum_i v_i W_16^i
+      float2 s0 = v[0], s1 = v[0];
+#pragma unroll
+      for (int i = 1; i < 16; ++i) {
+        s0 = cadd(s0, v[i]);
+        s1 = cadd(s1, twmul<false>(v[i], tw[i * (NMAX / 16)]));
+      }
+      work[row * P + pad16(j)] = s0;
+      work[row * P + pad16(j + 16)] = s1;
+    } else {
+      Dft<16, false, float2>::run(v);
+#pragma unroll
+      for (int k = 0; k < 16; ++k)
+        if (k < nz) work[row * P + pad16(j + 16 * k)] = v[k];
+    }
+    __syncwarp();
+  }
+
+  // inverse first stage, inputs j + 16 i for i < nz only
+  __device__ __forceinline__ void sq_inv1(int nz) {
+    int row, j;
+    sq_rowj(row, j);
+    float2 v[16];
+    if (nz <= 2) {
+      const float2 a = work[row * P + pad16(j)];
+      const float2 b = (nz == 2) ? work[row * P + pad16(j + 16)] : make_float2(0.f, 0.f);
+      __syncwarp();
+#pragma unroll
+      for (int k = 0; k < 16; ++k) v[k] = cadd(a, twmul<true>(b, tw[k * (NMAX / 16)]));
+    } else {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = (i < nz) ? work[row * P + pad16(j + 16 * i)] : make_float2(0.f, 0.f);
+      __syncwarp();
+      Dft<16, true, float2>::run(v);
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) work[row * P + pad16(16 * j + k)] = v[k];
+    __syncwarp();
+  }
+
+  // inverse second stage, the epilogue on its 16 outputs, and (unless last) the next
+  // iteration's forward first stage on the 16 new inputs, all in registers
+  template <typename Epi>
+  __device__ __forceinline__ void sq_inv2_epi_fwd1(Epi&& epi, bool next) {
+    int row, j;
+    sq_rowj(row, j);
+    float2 v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = work[row * P + pad16(j + 16 * i)];
+    __syncwarp();
+#pragma unroll
+    for (int i = 1; i < 16; ++i) v[i] = twmul<true>(v[i], tw[i * j * (NMAX / 256)]);
+    Dft<16, true, float2>::run(v);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = epi(row, j + 16 * i, v[i]);
+    if (next) {
+      Dft<16, false, float2>::run(v);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) work[row * P + pad16(16 * j + k)] = v[k];
+    }
+    __syncwarp();
+  }
+
+  // ---------------------------------------------------------------------------------------
   // cross-group radix-Q stage, Fourier-domain update, inverse radix-Q stage (in place)
   // ---------------------------------------------------------------------------------------
   __device__ __forceinline__ void middle(const uint32_t* peer, const float* mult_g, const float2* bt_g, int kc) {
@@ -429,49 +538,72 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
   __syncthreads();
 
   const bool fista = (a.beta != nullptr) && !ADMM;
-  for (int it = 0; it < a.iters; ++it) {
-    const float beta = fista ? __ldg(&a.beta[it]) : 0.0f;
-    const bool last = (it == a.iters - 1);
 
-    cta.template row_fft_from<0, false>(
-        [&](int row, int e, float2 x) {
-          if (e < kc) cta.work[row * P + pad16(e)] = x;
-        },
-        L1);
-    __syncthreads();
-    cta.template col_dft<false>(kc);
-    cluster_barrier<C>();
-    cta.middle(peer, mult, bt, kc);
-    cluster_barrier<C>();
-    cta.template col_dft<true>(kc);
-    __syncthreads();
-    cta.template row_fft_from<0, true>([&](int row, int e, float2 g) {
-      const int sidx = row * L1 + e;
-      if constexpr (!ADMM) {
-        const float2 c_old = cta.s0[sidx];
-        const float2 x = fista ? cta.s1[sidx] : c_old;  // z^(t)
-        const float2 un = make_float2(x.x - g.x, x.y - g.y);
-        const float2 cn = soft_threshold(un, kappa);
-        cta.s0[sidx] = cn;
-        if (fista) {
-          const float2 zn = make_float2(cn.x + beta * (cn.x - c_old.x), cn.y + beta * (cn.y - c_old.y));
-          cta.s1[sidx] = zn;
-          cta.work[row * P + pad16(e)] = zn;
-        } else {
-          cta.work[row * P + pad16(e)] = cn;
-        }
-      } else {
-        const float2 zo = cta.s0[sidx];
-        const float2 vo = cta.s1[sidx];
-        const float2 un = make_float2(zo.x - g.x, zo.y - g.y);  // c^(t+1) + v^(t)
-        const float2 zn = soft_threshold(un, kappa);
-        const float2 vn = make_float2(un.x - zn.x, un.y - zn.y);
-        cta.s0[sidx] = zn;
-        cta.s1[sidx] = vn;
-        cta.work[row * P + pad16(e)] = make_float2(zn.x - vn.x, zn.y - vn.y);
-        if (last && aux_out) aux_out[(crank + C * row) * L1 + e] = make_float2(un.x - vo.x, un.y - vo.y);
+  // The pointwise update of one element after the inverse transform: returns the
+  // next iteration's FFT input (z for ISTA/FISTA, z - v for ADMM).
+  auto update = [&](int row, int e, float2 g, float beta, bool last) -> float2 {
+    const int sidx = row * L1 + e;
+    if constexpr (!ADMM) {
+      const float2 c_old = cta.s0[sidx];
+      const float2 x = fista ? cta.s1[sidx] : c_old;  // z^(t)
+      const float2 un = make_float2(x.x - g.x, x.y - g.y);
+      const float2 cn = soft_threshold(un, kappa);
+      cta.s0[sidx] = cn;
+      if (fista) {
+        const float2 zn = make_float2(cn.x + beta * (cn.x - c_old.x), cn.y + beta * (cn.y - c_old.y));
+        cta.s1[sidx] = zn;
+        return zn;
       }
-    }, kc);
+      return cn;
+    } else {
+      const float2 zo = cta.s0[sidx];
+      const float2 vo = cta.s1[sidx];
+      const float2 un = make_float2(zo.x - g.x, zo.y - g.y);  // c^(t+1) + v^(t)
+      const float2 zn = soft_threshold(un, kappa);
+      const float2 vn = make_float2(un.x - zn.x, un.y - zn.y);
+      cta.s0[sidx] = zn;
+      cta.s1[sidx] = vn;
+      if (last && aux_out) aux_out[(crank + C * row) * L1 + e] = make_float2(un.x - vo.x, un.y - vo.y);
+      return make_float2(zn.x - vn.x, zn.y - vn.y);
+    }
+  };
+
+  if constexpr (S::SQ16) {
+    const int nz = kc / 16;
+    cta.sq_fwd1_from_work();
+    for (int it = 0; it < a.iters; ++it) {
+      const float beta = fista ? __ldg(&a.beta[it]) : 0.0f;
+      const bool last = (it == a.iters - 1);
+      cta.sq_fwd2(nz);
+      __syncthreads();
+      cta.template col_dft<false>(kc);
+      cluster_barrier<C>();
+      cta.middle(peer, mult, bt, kc);
+      cluster_barrier<C>();
+      cta.template col_dft<true>(kc);
+      __syncthreads();
+      cta.sq_inv1(nz);
+      cta.sq_inv2_epi_fwd1([&](int row, int e, float2 g) { return update(row, e, g, beta, last); }, !last);
+    }
+  } else {
+    for (int it = 0; it < a.iters; ++it) {
+      const float beta = fista ? __ldg(&a.beta[it]) : 0.0f;
+      const bool last = (it == a.iters - 1);
+      cta.template row_fft_from<0, false>(
+          [&](int row, int e, float2 x) {
+            if (e < kc) cta.work[row * P + pad16(e)] = x;
+          },
+          L1);
+      __syncthreads();
+      cta.template col_dft<false>(kc);
+      cluster_barrier<C>();
+      cta.middle(peer, mult, bt, kc);
+      cluster_barrier<C>();
+      cta.template col_dft<true>(kc);
+      __syncthreads();
+      cta.template row_fft_from<0, true>(
+          [&](int row, int e, float2 g) { cta.work[row * P + pad16(e)] = update(row, e, g, beta, last); }, kc);
+    }
   }
 
   // ---- write the result

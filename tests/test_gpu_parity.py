@@ -109,6 +109,19 @@ def test_shapes(lib, algo, L1, L2):
     assert_parity(run["c"][0], ref, what=f"{algo} {L1}x{L2}")
 
 
+@pytest.mark.parametrize("algo", ["fista", "admm"])
+@pytest.mark.parametrize("M1,L2", [(8, 32), (16, 64), (30, 32), (48, 128), (100, 32), (300, 16)])
+def test_row256_active_column_counts(lib, algo, M1, L2):
+    """Rows of 256 use a specialised transform whose work depends on how many 16-wide
+    blocks of Fourier columns the element mask reaches (1, 2, 3, 7 and all 16; the
+    last two masks are wider than the grid and fold)."""
+    M2 = 4
+    s = _snap(500 + M1 + L2, M1, M2, max(2, (M1 * M2) // 5), 256, L2, K=3, snr=15.0, lam_frac=0.08)
+    ref = oracle_run(s, algo, 100, rho=16.0)
+    run = gpu_run(lib, [s], [ref["lam"]], algo, 100, rho=16.0)
+    assert_parity(run["c"][0], ref, what=f"{algo} M1={M1} 256x{L2}")
+
+
 # ------------------------------------------------------------------------------------------
 # batched, ragged shapes in one call
 # ------------------------------------------------------------------------------------------
