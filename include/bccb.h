@@ -142,6 +142,24 @@ int bccb_batch_replay(bccb_solver_t s);
 int bccb_batch_tune(bccb_solver_t s, const void* y_dev, int probe_iters, const char* cache_path);
 int bccb_batch_tile(bccb_solver_t s, int L1, int L2, int* tile);
 
+/* Unrolled FISTA network (a learned extension of eq:fista; the paper has no learned
+ * part).  On a FISTA solver, layer k = 0..layers-1 runs
+ *     u_k = z_k - a_k mu (G z_k - b),  c_k = S_{t_k mu lam}(u_k),  z_{k+1} = c_k + beta_k (c_k - c_{k-1})
+ * with z_0 = c_{-1} = 0, FISTA's beta_k, and per-layer multipliers a_k = scale_dev[k],
+ * t_k = thresh_dev[k] (device float arrays; a = t = 1 is plain FISTA with `layers`
+ * iterations).  bccb_unrolled_fwd runs the setup and the layers, writes c_{K-1} to
+ * c_out_dev, and, if saved_dev is not NULL, stores each layer's input z_k and
+ * mu (G z_k - b) there (layers * 2 * (packed solution length) complex64 values) for
+ * the backward pass; check != 0 runs the FP64 KKT check on c_{K-1}.
+ * bccb_unrolled_bwd takes grad_c_dev = dLoss/dc_{K-1} (complex64, packed like c, as
+ * dLoss/dRe + j dLoss/dIm) and ADDS dLoss/da_k and dLoss/dt_k, summed over the batch,
+ * to the device float64 arrays grad_scale_dev / grad_thresh_dev (length layers).  It
+ * needs the same solver, layers, multipliers and saved buffer as the forward call. */
+int bccb_unrolled_fwd(bccb_solver_t s, const void* y_dev, int layers, const float* scale_dev,
+                      const float* thresh_dev, void* c_out_dev, void* saved_dev, int check);
+int bccb_unrolled_bwd(bccb_solver_t s, int layers, const float* scale_dev, const float* thresh_dev,
+                      const void* saved_dev, const void* grad_c_dev, double* grad_scale_dev, double* grad_thresh_dev);
+
 /* Phase timing of bccb_batch_solve, for profiling.  bccb_set_timing(s, 1) makes
  * every later solve record CUDA events on the solver's stream around its three
  * phases; bccb_last_timing synchronises and returns the last solve's setup,

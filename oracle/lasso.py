@@ -82,7 +82,7 @@ def soft_threshold(u: np.ndarray, kappa: float) -> np.ndarray:
 def step_size(A: np.ndarray) -> float:
     """mu = 1 / sigma_max(A)^2 (eq:ista); sigma_max^2 is the top eigenvalue of A A^H."""
     AAh = A @ A.conj().T
-    top = scipy.linalg.eigvalsh(AAh, subset_by_index=[AAh.shape[0] - 1, AAh.shape[0] - 1])[0]
+    top = np.linalg.eigvalsh(AAh)[-1]  # ascending eigenvalues of the Hermitian N x N matrix
     return 1.0 / float(top)
 
 

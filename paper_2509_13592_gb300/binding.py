@@ -58,6 +58,8 @@ def _load():
     lib.bccb_batch_replay.argtypes = [vp]
     lib.bccb_batch_tune.argtypes = [vp, vp, i32, ctypes.c_char_p]
     lib.bccb_batch_tile.argtypes = [vp, i32, i32, P(i32)]
+    lib.bccb_unrolled_fwd.argtypes = [vp, vp, i32, vp, vp, vp, vp, i32]
+    lib.bccb_unrolled_bwd.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp]
     lib.bccb_batch_size.argtypes = [vp, P(i32)]
     lib.bccb_instance_shape.argtypes = [vp, i32, P(i32), P(i32), P(i32)]
     lib.bccb_destroy.argtypes = [vp]
@@ -68,7 +70,7 @@ def _load():
     for name in ("bccb_batch_create", "bccb_batch_solve", "bccb_batch_solve_host", "bccb_batch_results",
                  "bccb_batch_get", "bccb_create", "bccb_solve", "bccb_batch_size", "bccb_instance_shape",
                  "bccb_destroy", "bccb_set_timing", "bccb_last_timing", "bccb_batch_capture", "bccb_batch_replay",
-                 "bccb_batch_tune", "bccb_batch_tile"):
+                 "bccb_batch_tune", "bccb_batch_tile", "bccb_unrolled_fwd", "bccb_unrolled_bwd"):
         getattr(lib, name).restype = i32
     return lib
 
@@ -182,6 +184,18 @@ def bccb_batch_tile(h: int, L1: int, L2: int) -> int:
     t = ctypes.c_int(0)
     _raise(_lib.bccb_batch_tile(h, int(L1), int(L2), ctypes.byref(t)), h)
     return t.value
+
+
+def bccb_unrolled_fwd(h: int, y_dev, layers: int, scale_dev, thresh_dev, c_out_dev, saved_dev=None,
+                      check: bool = False) -> None:
+    _raise(_lib.bccb_unrolled_fwd(h, _ptr(y_dev), int(layers), _ptr(scale_dev), _ptr(thresh_dev), _ptr(c_out_dev),
+                                  _ptr(saved_dev), 1 if check else 0), h)
+
+
+def bccb_unrolled_bwd(h: int, layers: int, scale_dev, thresh_dev, saved_dev, grad_c_dev, grad_scale_dev,
+                      grad_thresh_dev) -> None:
+    _raise(_lib.bccb_unrolled_bwd(h, int(layers), _ptr(scale_dev), _ptr(thresh_dev), _ptr(saved_dev),
+                                  _ptr(grad_c_dev), _ptr(grad_scale_dev), _ptr(grad_thresh_dev)), h)
 
 
 def bccb_set_timing(h: int, enable: bool) -> None:

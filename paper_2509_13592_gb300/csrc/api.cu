@@ -236,7 +236,7 @@ int bccb_batch_solve(bccb_solver_t s, const void* y_dev, int iters, const void* 
   const float2* y = reinterpret_cast<const float2*>(y_dev);
   BCCB_CUDA(s, bccb::run_setup(s, y));
   if (s->timing) BCCB_CUDA(s, cudaEventRecordWithFlags(s->ev[1], s->stream, cudaEventRecordExternal));
-  FusedArgs a;
+  FusedArgs a{};
   a.insts = s->d_fused;
   a.beta = (s->algo == BCCB_FISTA) ? s->d_beta : nullptr;
   a.twiddle = s->d_tw32;
@@ -459,7 +459,7 @@ int bccb_batch_tune(bccb_solver_t s, const void* y_dev, int probe_iters, const c
         continue;
       }
     }
-    FusedArgs a;
+    FusedArgs a{};
     a.insts = s->d_fused;
     a.ids = s->d_ids + c.first;
     a.beta = (s->algo == BCCB_FISTA) ? s->d_beta : nullptr;
@@ -500,6 +500,72 @@ int bccb_batch_tune(bccb_solver_t s, const void* y_dev, int probe_iters, const c
     s->graph = nullptr;
   }
   if (status != BCCB_OK) return fail(s, status, "preparing a cached tile failed");
+  return BCCB_OK;
+}
+
+int bccb_unrolled_fwd(bccb_solver_t s, const void* y_dev, int layers, const float* scale_dev,
+                      const float* thresh_dev, void* c_out_dev, void* saved_dev, int check) {
+  if (!s) return fail(nullptr, BCCB_ERR_INVALID_ARG, "solver is NULL");
+  s->last_error.clear();
+  if (s->algo != BCCB_FISTA) return fail(s, BCCB_ERR_INVALID_ARG, "the unrolled network needs a FISTA solver");
+  if (!y_dev || !c_out_dev || !scale_dev || !thresh_dev || layers < 1)
+    return fail(s, BCCB_ERR_INVALID_ARG, "bad y, c_out, scale, thresh or layers");
+  BCCB_CUDA(s, cudaSetDevice(s->device));
+  s->launches = 0;
+  BCCB_CUDA(s, bccb::fista_schedule(s, layers));
+  const float2* y = reinterpret_cast<const float2*>(y_dev);
+  BCCB_CUDA(s, bccb::run_setup(s, y));
+  FusedArgs a{};
+  a.insts = s->d_fused;
+  a.beta = s->d_beta;
+  a.twiddle = s->d_tw32;
+  a.mult = s->d_mult;
+  a.bt = s->d_cterm;
+  a.c_out = reinterpret_cast<float2*>(c_out_dev);
+  a.scale = scale_dev;
+  a.thresh = thresh_dev;
+  a.save = reinterpret_cast<float2*>(saved_dev);
+  a.save_stride = s->total_c;
+  a.iters = layers;
+  for (const auto& c : s->classes) {
+    a.ids = s->d_ids + c.first;
+    BCCB_CUDA(s, c.entry.launch(a, c.count, s->stream));
+    s->launches += 1;
+  }
+  if (check) BCCB_CUDA(s, bccb::run_check(s, y, reinterpret_cast<const float2*>(c_out_dev)));
+  s->last_checked = check != 0;
+  return BCCB_OK;
+}
+
+int bccb_unrolled_bwd(bccb_solver_t s, int layers, const float* scale_dev, const float* thresh_dev,
+                      const void* saved_dev, const void* grad_c_dev, double* grad_scale_dev, double* grad_thresh_dev) {
+  if (!s) return fail(nullptr, BCCB_ERR_INVALID_ARG, "solver is NULL");
+  s->last_error.clear();
+  if (s->algo != BCCB_FISTA) return fail(s, BCCB_ERR_INVALID_ARG, "the unrolled network needs a FISTA solver");
+  if (!scale_dev || !thresh_dev || !saved_dev || !grad_c_dev || !grad_scale_dev || !grad_thresh_dev || layers < 1)
+    return fail(s, BCCB_ERR_INVALID_ARG, "bad pointer or layers");
+  if (s->beta_len < layers) return fail(s, BCCB_ERR_INVALID_ARG, "run bccb_unrolled_fwd with these layers first");
+  BCCB_CUDA(s, cudaSetDevice(s->device));
+  bccb::AdjArgs a{};
+  a.insts = s->d_fused;
+  a.beta = s->d_beta;
+  a.twiddle = s->d_tw32;
+  a.mult = s->d_mult;
+  a.scale = scale_dev;
+  a.thresh = thresh_dev;
+  a.save = reinterpret_cast<const float2*>(saved_dev);
+  a.save_stride = s->total_c;
+  a.grad_c = reinterpret_cast<const float2*>(grad_c_dev);
+  a.grad_scale = grad_scale_dev;
+  a.grad_thresh = grad_thresh_dev;
+  a.layers = layers;
+  for (const auto& c : s->classes) {
+    const bccb::AdjointEntry* ae = bccb::adjoint_lookup(c.entry.L1, c.entry.L2);
+    if (!ae) return fail(s, BCCB_ERR_UNSUPPORTED, "no adjoint kernel for this grid");
+    BCCB_CUDA(s, ae->prepare());
+    a.ids = s->d_ids + c.first;
+    BCCB_CUDA(s, ae->launch(a, c.count, s->stream));
+  }
   return BCCB_OK;
 }
 

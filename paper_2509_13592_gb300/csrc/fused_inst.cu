@@ -2,6 +2,7 @@
 // length L1 in {16, 32, 64, 128, 256}, with the 8192-element tile and, for grids of
 // at least 8192 elements, the 4096-element tile (twice the CTAs per cluster); the
 // build compiles this file once per L2.
+#include "adjoint.cuh"
 #include "solver.h"
 
 #ifndef BCCB_L2
@@ -36,6 +37,15 @@ const FusedEntry* BCCB_CAT(fused_lookup_L2_, BCCB_L2)(int L1, bool admm, int til
   };
   for (const FusedEntry& e : table)
     if (e.L1 == L1 && e.admm == (admm ? 1 : 0) && e.tile == tile) return &e;
+  return nullptr;
+}
+
+const AdjointEntry* BCCB_CAT(adjoint_lookup_L2_, BCCB_L2)(int L1) {
+  static const AdjointEntry table[] = {adjoint_entry<16, BCCB_L2>(), adjoint_entry<32, BCCB_L2>(),
+                                       adjoint_entry<64, BCCB_L2>(), adjoint_entry<128, BCCB_L2>(),
+                                       adjoint_entry<256, BCCB_L2>()};
+  for (const AdjointEntry& e : table)
+    if (e.L1 == L1) return &e;
   return nullptr;
 }
 

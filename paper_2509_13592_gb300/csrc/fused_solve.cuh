@@ -60,6 +60,13 @@ struct FusedArgs {
   const float2* c0;        // warm start (z^(0) for ADMM) or nullptr for zeros
   float2* c_out;           // c^(T) (ISTA/FISTA) or z^(T) (ADMM)
   float2* aux_out;         // ADMM only: c^(T); nullable
+  // unrolled network (all nullable): iteration t uses u = x - scale[t] * G' and the
+  // threshold thresh[t] * kappa, and stores its input z^(t) and G' into
+  // save[(2t) * save_stride + c] and save[(2t + 1) * save_stride + c]
+  const float* scale;
+  const float* thresh;
+  float2* save;
+  int64_t save_stride;
   int iters;
   int pad_;
 };
@@ -377,6 +384,21 @@ struct FusedCta {
     __syncwarp();
   }
 
+  // twiddles and the per-pair frequency masks (bt may be null: a Gram product alone)
+  __device__ __forceinline__ void load_tables(const float2* twiddle, const float* mult, const float2* bt) {
+    for (int e = tid; e < NMAX; e += T) tw[e] = twiddle[e * (kTwiddleLen / NMAX)];
+    for (int pl = tid; pl < SH; pl += T) {
+      const int p = crank * SH + pl;
+      const int k1 = p / L1, col = p % L1;
+      uint32_t pm = 0;
+      for (int q = 0; q < Q; ++q) {
+        const int f = (k1 + RP * q) * L1 + col;
+        if (mult[f] != 0.f || (bt && (bt[f].x != 0.f || bt[f].y != 0.f))) pm |= 1u << q;
+      }
+      pmask[pl] = (uint16_t)pm;
+    }
+  }
+
   // ---------------------------------------------------------------------------------------
   // cross-group radix-Q stage, Fourier-domain update, inverse radix-Q stage (in place)
   // ---------------------------------------------------------------------------------------
@@ -399,13 +421,13 @@ struct FusedCta {
           const int q1 = rest ? __ffs(rest) - 1 : -1;
           const int f0 = (k1 + RP * q0) * L1 + col;
           const float m0 = ld_ro_f32(&mult_g[f0]);
-          const float2 b0 = ld_ro_f32x2(&bt_g[f0]);
+          const float2 b0 = bt_g ? ld_ro_f32x2(&bt_g[f0]) : make_float2(0.f, 0.f);
           float m1 = 0.f;
           float2 b1 = make_float2(0.f, 0.f);
           if (q1 >= 0) {
             const int f1 = (k1 + RP * q1) * L1 + col;
             m1 = ld_ro_f32(&mult_g[f1]);
-            b1 = ld_ro_f32x2(&bt_g[f1]);
+            if (bt_g) b1 = ld_ro_f32x2(&bt_g[f1]);
           }
 #pragma unroll
           for (int g = 0; g < Q; ++g) {
@@ -434,7 +456,7 @@ struct FusedCta {
               } else {
                 const int f = (k1 + RP * q) * L1 + col;
                 m = ld_ro_f32(&mult_g[f]);
-                b = ld_ro_f32x2(&bt_g[f]);
+                b = bt_g ? ld_ro_f32x2(&bt_g[f]) : make_float2(0.f, 0.f);
               }
               v[q] = make_float2(v[q].x * m - b.x, v[q].y * m - b.y);
             } else {
@@ -516,17 +538,7 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
   }
 
   // ---- load twiddles, the frequency masks and the initial state
-  for (int e = threadIdx.x; e < NMAX; e += T) cta.tw[e] = a.twiddle[e * (kTwiddleLen / NMAX)];
-  for (int pl = threadIdx.x; pl < SH; pl += T) {
-    const int p = crank * SH + pl;
-    const int k1 = p / L1, col = p % L1;
-    uint32_t pm = 0;
-    for (int q = 0; q < Q; ++q) {
-      const int f = (k1 + RP * q) * L1 + col;
-      if (mult[f] != 0.f || bt[f].x != 0.f || bt[f].y != 0.f) pm |= 1u << q;
-    }
-    cta.pmask[pl] = (uint16_t)pm;
-  }
+  cta.load_tables(a.twiddle, mult, bt);
   for (int idx = threadIdx.x; idx < E; idx += T) {
     const int s = idx / L1, e = idx % L1;
     const int gidx = (crank + C * s) * L1 + e;
@@ -541,13 +553,18 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
 
   // The pointwise update of one element after the inverse transform: returns the
   // next iteration's FFT input (z for ISTA/FISTA, z - v for ADMM).
-  auto update = [&](int row, int e, float2 g, float beta, bool last) -> float2 {
+  auto update = [&](int row, int e, float2 g, float beta, bool last, float sc, float kap, float2* save_t) -> float2 {
     const int sidx = row * L1 + e;
     if constexpr (!ADMM) {
       const float2 c_old = cta.s0[sidx];
       const float2 x = fista ? cta.s1[sidx] : c_old;  // z^(t)
-      const float2 un = make_float2(x.x - g.x, x.y - g.y);
-      const float2 cn = soft_threshold(un, kappa);
+      if (save_t) {
+        const int gidx = (crank + C * row) * L1 + e;
+        save_t[gidx] = x;
+        save_t[a.save_stride + gidx] = g;
+      }
+      const float2 un = make_float2(x.x - sc * g.x, x.y - sc * g.y);
+      const float2 cn = soft_threshold(un, kap);
       cta.s0[sidx] = cn;
       if (fista) {
         const float2 zn = make_float2(cn.x + beta * (cn.x - c_old.x), cn.y + beta * (cn.y - c_old.y));
@@ -559,13 +576,21 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
       const float2 zo = cta.s0[sidx];
       const float2 vo = cta.s1[sidx];
       const float2 un = make_float2(zo.x - g.x, zo.y - g.y);  // c^(t+1) + v^(t)
-      const float2 zn = soft_threshold(un, kappa);
+      const float2 zn = soft_threshold(un, kap);
       const float2 vn = make_float2(un.x - zn.x, un.y - zn.y);
       cta.s0[sidx] = zn;
       cta.s1[sidx] = vn;
       if (last && aux_out) aux_out[(crank + C * row) * L1 + e] = make_float2(un.x - vo.x, un.y - vo.y);
+      (void)sc;
+      (void)save_t;
       return make_float2(zn.x - vn.x, zn.y - vn.y);
     }
+  };
+  // per-iteration multipliers of the unrolled network (1 and kappa otherwise)
+  auto layer = [&](int it, float& sc, float& kap, float2*& save_t) {
+    sc = a.scale ? __ldg(&a.scale[it]) : 1.0f;
+    kap = a.thresh ? __ldg(&a.thresh[it]) * kappa : kappa;
+    save_t = a.save ? a.save + (int64_t)(2 * it) * a.save_stride + in.c_off : nullptr;
   };
 
   if constexpr (S::SQ16) {
@@ -583,7 +608,11 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
       cta.template col_dft<true>(kc);
       __syncthreads();
       cta.sq_inv1(nz);
-      cta.sq_inv2_epi_fwd1([&](int row, int e, float2 g) { return update(row, e, g, beta, last); }, !last);
+      float sc, kap;
+      float2* save_t;
+      layer(it, sc, kap, save_t);
+      cta.sq_inv2_epi_fwd1(
+          [&](int row, int e, float2 g) { return update(row, e, g, beta, last, sc, kap, save_t); }, !last);
     }
   } else {
     for (int it = 0; it < a.iters; ++it) {
@@ -601,8 +630,14 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
       cluster_barrier<C>();
       cta.template col_dft<true>(kc);
       __syncthreads();
+      float sc, kap;
+      float2* save_t;
+      layer(it, sc, kap, save_t);
       cta.template row_fft_from<0, true>(
-          [&](int row, int e, float2 g) { cta.work[row * P + pad16(e)] = update(row, e, g, beta, last); }, kc);
+          [&](int row, int e, float2 g) {
+            cta.work[row * P + pad16(e)] = update(row, e, g, beta, last, sc, kap, save_t);
+          },
+          kc);
     }
   }
 

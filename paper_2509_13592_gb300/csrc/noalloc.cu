@@ -194,7 +194,7 @@ extern "C" int bccb_solve_noalloc(int M1, int M2, const uint8_t* mask_dev, int L
   if ((e = bccb::run_setup(&s, reinterpret_cast<const float2*>(y_dev))) != cudaSuccess)
     return reject(BCCB_ERR_CUDA, cudaGetErrorString(e));
   if ((e = fe->prepare()) != cudaSuccess) return reject(BCCB_ERR_CUDA, cudaGetErrorString(e));
-  bccb::FusedArgs a;
+  bccb::FusedArgs a{};
   a.insts = s.d_fused;
   a.ids = s.d_ids;
   a.beta = (algo == BCCB_FISTA) ? s.d_beta : nullptr;

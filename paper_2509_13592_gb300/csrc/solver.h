@@ -7,7 +7,7 @@
 #include <string>
 #include <vector>
 
-#include "fused_solve.cuh"
+#include "adjoint.cuh"
 
 namespace bccb {
 
@@ -101,4 +101,5 @@ cudaError_t fista_schedule(bccb_solver* s, int iters);
 cudaError_t prepare_fp64_passes(int max_L2);
 // fused_inst.cu / fused_dispatch.cu: tile 0 = the default 8192-element tile
 const FusedEntry* fused_lookup(int L1, int L2, bool admm, int tile = 0);
+const AdjointEntry* adjoint_lookup(int L1, int L2);
 }  // namespace bccb
