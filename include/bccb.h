@@ -21,8 +21,10 @@
  *   c      complex64, L1*L2 entries stored as an L2 x L1 row-major grid: entry
  *          l1 + l2*L1 is the amplitude at harmonics (f_{1,l1}, f_{2,l2}) with
  *          f_{i,l} = -1/2 + l/L_i (Section II-A: column l1 + l2 L1 of D).
- * Supported grids: L1, L2 powers of two in [16, 256]; M1, M2 >= 1 (masks wider
- * than the grid fold, which the BCCB structure allows).
+ * Supported grids: L1, L2 powers of two in [16, 1024]; M1, M2 >= 1 (masks wider
+ * than the grid fold, which the BCCB structure allows).  FP32 grids up to 256 x 256
+ * run on chip (one thread-block cluster per instance); larger grids and the FP64
+ * path run as two passes per iteration over L2-resident global memory.
  *
  * Conventions
  *   * Every call returns a status (BCCB_OK = 0).  No exception crosses the ABI and
@@ -50,6 +52,9 @@ typedef struct bccb_solver* bccb_solver_t;
 /* Algorithms (Section II-B). */
 enum { BCCB_ISTA = 0, BCCB_FISTA = 1, BCCB_ADMM = 2 };
 
+/* Arithmetic of the iterations: complex64 (y, c complex64) or complex128 (y, c complex128). */
+enum { BCCB_F32 = 0, BCCB_F64 = 1 };
+
 /* Status codes. */
 enum {
   BCCB_OK = 0,
@@ -64,7 +69,7 @@ enum {
  * mask buffer (bytes), one y buffer and one c buffer (complex elements). */
 typedef struct {
   int32_t M1, M2;      /* URA size (Section II-A) */
-  int32_t L1, L2;      /* harmonic grid lengths (powers of two, 16..256) */
+  int32_t L1, L2;      /* harmonic grid lengths (powers of two, 16..1024) */
   int64_t mask_off;    /* byte offset of this instance's M1*M2 mask in masks_host */
   int64_t y_off;       /* complex64 offset of this instance's N measurements */
   int64_t c_off;       /* complex64 offset of this instance's L1*L2 solution */
@@ -80,6 +85,11 @@ typedef struct {
  * reserved != 0), UNSUPPORTED (grid size), CUDA. */
 int bccb_batch_create(bccb_solver_t* out, const bccb_inst_t* insts, int n, const uint8_t* masks_host,
                       int algo, double rho, void* cuda_stream);
+/* As bccb_batch_create, with the arithmetic: BCCB_F32 (complex64 y and c) or
+ * BCCB_F64 (complex128 y and c in every call on this solver; the whole solve in
+ * FP64, the check path the FP32 results are compared with). */
+int bccb_batch_create2(bccb_solver_t* out, const bccb_inst_t* insts, int n, const uint8_t* masks_host,
+                       int algo, double rho, int prec, void* cuda_stream);
 
 /* Run the whole hot path for every instance on the solver's stream:
  *   setup (FP64): Lambda = FFT2 of the Gram's first column (eq:lambda),

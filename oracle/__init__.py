@@ -12,6 +12,8 @@ and what the tests check the two against.
 """
 from .lasso import (  # noqa: F401
     dictionary,
+    dictionary_columns,
+    adjoint_measurements_kron,
     harmonic_grid,
     element_positions,
     soft_threshold,

@@ -64,6 +64,28 @@ def dictionary(mask, M1: int, M2: int, L1: int, L2: int) -> np.ndarray:
     return A
 
 
+def dictionary_columns(mask, M1: int, M2: int, L1: int, L2: int, cols) -> np.ndarray:
+    """Columns `cols` (indices l1 + l2*L1) of D_s, shape (N, len(cols)): entry (n, l) =
+    D1(m1_n, l1) D2(m2_n, l2) (eq:subdictionary, eq:forward_model), for grids too large to
+    form whole."""
+    m1, m2 = element_positions(mask, M1)
+    cols = np.asarray(cols)
+    l1, l2 = cols % L1, cols // L1
+    f1, f2 = harmonic_grid(L1)[l1], harmonic_grid(L2)[l2]
+    return np.exp(-2j * np.pi * np.outer(m1, f1)) * np.exp(-2j * np.pi * np.outer(m2, f2))
+
+
+def adjoint_measurements_kron(mask, M1: int, M2: int, L1: int, L2: int, y) -> np.ndarray:
+    """b = A^H y for grids too large to form A, from D = D2 kron D1 (eq:forward_model): with the
+    kept rows D1s = D1[m1_n, :] (N x L1) and D2s = D2[m2_n, :] (N x L2),
+    b[l1 + l2 L1] = sum_n conj(D2s[n, l2]) y_n conj(D1s[n, l1]) = (D2s^H diag(y) conj(D1s))[l2, l1]."""
+    m1, m2 = element_positions(mask, M1)
+    D1s = np.exp(-2j * np.pi * np.outer(m1, harmonic_grid(L1)))
+    D2s = np.exp(-2j * np.pi * np.outer(m2, harmonic_grid(L2)))
+    y = np.asarray(y, np.complex128)
+    return (D2s.conj().T @ (y[:, None] * D1s.conj())).reshape(-1)
+
+
 # ------------------------------------------------------------------------------------------
 # Building blocks of Section II-B
 # ------------------------------------------------------------------------------------------

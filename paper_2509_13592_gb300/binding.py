@@ -17,6 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbccb.so")
 
 ISTA, FISTA, ADMM = 0, 1, 2
+F32, F64 = 0, 1
 ALGOS = {"ista": ISTA, "fista": FISTA, "admm": ADMM}
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_KKT, ERR_TIMEOUT = range(6)
 GET_LAMBDA, GET_B, GET_MULT, GET_CTERM = 0, 1, 2, 3
@@ -45,6 +46,7 @@ def _load():
     vp, i32, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
     P = ctypes.POINTER
     lib.bccb_batch_create.argtypes = [P(vp), P(bccb_inst_t), i32, vp, i32, dbl, vp]
+    lib.bccb_batch_create2.argtypes = [P(vp), P(bccb_inst_t), i32, vp, i32, dbl, i32, vp]
     lib.bccb_batch_solve.argtypes = [vp, vp, i32, vp, vp, vp, i32]
     lib.bccb_batch_solve_host.argtypes = [vp, vp, i32, vp, i32]
     lib.bccb_batch_results.argtypes = [vp, vp, vp, vp, vp]
@@ -67,7 +69,7 @@ def _load():
     lib.bccb_status_string.restype = ctypes.c_char_p
     lib.bccb_last_error.argtypes = [vp]
     lib.bccb_last_error.restype = ctypes.c_char_p
-    for name in ("bccb_batch_create", "bccb_batch_solve", "bccb_batch_solve_host", "bccb_batch_results",
+    for name in ("bccb_batch_create", "bccb_batch_create2", "bccb_batch_solve", "bccb_batch_solve_host", "bccb_batch_results",
                  "bccb_batch_get", "bccb_create", "bccb_solve", "bccb_batch_size", "bccb_instance_shape",
                  "bccb_destroy", "bccb_set_timing", "bccb_last_timing", "bccb_batch_capture", "bccb_batch_replay",
                  "bccb_batch_tune", "bccb_batch_tile", "bccb_unrolled_fwd", "bccb_unrolled_bwd"):
@@ -110,12 +112,12 @@ def _stream(stream) -> Optional[int]:
 
 
 def bccb_batch_create(insts: Sequence[bccb_inst_t], masks_host: np.ndarray, algo: int, rho: float = 1.0,
-                      stream=None) -> int:
+                      stream=None, prec: int = F32) -> int:
     arr = (bccb_inst_t * len(insts))(*insts)
     masks = np.ascontiguousarray(masks_host, dtype=np.uint8)
     h = ctypes.c_void_p()
-    st = _lib.bccb_batch_create(ctypes.byref(h), arr, len(insts), masks.ctypes.data_as(ctypes.c_void_p),
-                                int(algo), float(rho), _stream(stream))
+    st = _lib.bccb_batch_create2(ctypes.byref(h), arr, len(insts), masks.ctypes.data_as(ctypes.c_void_p),
+                                 int(algo), float(rho), int(prec), _stream(stream))
     _raise(st, None)
     return h.value
 
@@ -127,8 +129,8 @@ def bccb_batch_solve(h: int, y_dev, iters: int, c0_dev, c_out_dev, aux_out_dev=N
 
 def bccb_batch_solve_host(h: int, y_host: np.ndarray, iters: int, c_out_host: np.ndarray, check: bool = True) -> None:
     for a in (y_host, c_out_host):
-        if not (isinstance(a, np.ndarray) and a.flags.c_contiguous and a.dtype == np.complex64):
-            raise ValueError("host buffers must be C-contiguous complex64 numpy arrays")
+        if not (isinstance(a, np.ndarray) and a.flags.c_contiguous and a.dtype in (np.complex64, np.complex128)):
+            raise ValueError("host buffers must be C-contiguous complex numpy arrays of the solver's precision")
     _raise(_lib.bccb_batch_solve_host(h, y_host.ctypes.data_as(ctypes.c_void_p), int(iters),
                                       c_out_host.ctypes.data_as(ctypes.c_void_p), 1 if check else 0), h)
 
@@ -228,9 +230,9 @@ def bccb_status_string(status: int) -> str:
 # ------------------------------------------------------------------------------------------
 
 
-def pack(instances):
+def pack(instances, dtype=np.complex64):
     """Pack instances given as dicts with keys M1, M2, L1, L2, mask (uint8, M1*M2),
-    y (complex, N), lam, lam_is_frac into (inst table, masks, y complex64, total c).
+    y (complex, N), lam, lam_is_frac into (inst table, masks, y of `dtype`, total c).
 
     Instance i's measurements start at y_off = sum of previous N; its solution at
     c_off = sum of previous L1*L2.
@@ -244,7 +246,7 @@ def pack(instances):
                         1 if d.get("lam_is_frac", False) else 0, 0)
         insts.append(q)
         masks.append(mask)
-        ys.append(y.astype(np.complex64))
+        ys.append(y.astype(dtype))
         m_off += mask.size
         y_off += y.size
         c_off += d["L1"] * d["L2"]
@@ -254,12 +256,14 @@ def pack(instances):
 class BatchSolver:
     """Owns one solver handle.  ``instances`` as for :func:`pack`."""
 
-    def __init__(self, instances, algo="fista", rho: float = 1.0, stream=None):
+    def __init__(self, instances, algo="fista", rho: float = 1.0, stream=None, prec="f32"):
         self.algo = ALGOS[algo] if isinstance(algo, str) else int(algo)
-        self.insts, self.masks, self.y_host, self.total_c = pack(instances)
+        self.prec = {"f32": F32, "f64": F64}[prec] if isinstance(prec, str) else int(prec)
+        self.dtype = np.complex128 if self.prec == F64 else np.complex64
+        self.insts, self.masks, self.y_host, self.total_c = pack(instances, self.dtype)
         self.n = len(self.insts)
         self.offsets = [(q.c_off, q.L1, q.L2) for q in self.insts]
-        self.handle = bccb_batch_create(self.insts, self.masks, self.algo, rho, stream)
+        self.handle = bccb_batch_create(self.insts, self.masks, self.algo, rho, stream, self.prec)
 
     def solve(self, y_dev, iters, c_out, c0=None, aux_out=None, check=True):
         bccb_batch_solve(self.handle, y_dev, iters, c0, c_out, aux_out, check)

@@ -59,9 +59,10 @@ void release_streams(bccb_solver* s) {
 
 void release(bccb_solver* s) {
   release_streams(s);
-  void* ptrs[] = {s->d_desc, s->d_mask_idx, s->d_lam64, s->d_b64,  s->d_w64,    s->d_mult,    s->d_cterm,
-                  s->d_par,  s->d_fused,    s->d_ids,   s->d_beta, s->d_kkt,    s->d_obj,     s->d_red,
-                  s->d_tw32, s->d_tw64,     s->d_y_stage, s->d_c_stage};
+  void* ptrs[] = {s->d_desc,   s->d_mask_idx, s->d_lam64,   s->d_b64,     s->d_w64,     s->d_mult,
+                  s->d_cterm,  s->d_par,      s->d_fused,   s->d_ids,     s->d_beta,    s->d_beta64,
+                  s->d_kkt,    s->d_obj,      s->d_red,     s->d_tw32,    s->d_tw64,    s->d_y_stage,
+                  s->d_c_stage, s->d_mult64,  s->d_bt64,    s->d_mp_work, s->d_mp_s0,   s->d_mp_s1};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -86,6 +87,11 @@ const char* bccb_last_error(bccb_solver_t s) { return s ? s->last_error.c_str() 
 
 int bccb_batch_create(bccb_solver_t* out, const bccb_inst_t* insts, int n, const uint8_t* masks_host, int algo,
                       double rho, void* cuda_stream) {
+  return bccb_batch_create2(out, insts, n, masks_host, algo, rho, BCCB_F32, cuda_stream);
+}
+
+int bccb_batch_create2(bccb_solver_t* out, const bccb_inst_t* insts, int n, const uint8_t* masks_host, int algo,
+                       double rho, int prec, void* cuda_stream) {
   g_create_error.clear();
   if (!out) return fail(nullptr, BCCB_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
@@ -93,9 +99,11 @@ int bccb_batch_create(bccb_solver_t* out, const bccb_inst_t* insts, int n, const
   if (algo != BCCB_ISTA && algo != BCCB_FISTA && algo != BCCB_ADMM)
     return fail(nullptr, BCCB_ERR_INVALID_ARG, "algo must be ISTA, FISTA or ADMM");
   if (algo == BCCB_ADMM && !(rho > 0.0)) return fail(nullptr, BCCB_ERR_INVALID_ARG, "ADMM needs rho > 0");
+  if (prec != BCCB_F32 && prec != BCCB_F64) return fail(nullptr, BCCB_ERR_INVALID_ARG, "prec must be F32 or F64");
 
   bccb_solver* s = new bccb_solver;
   s->n = n;
+  s->prec = prec;
   s->algo = algo;
   s->rho = (algo == BCCB_ADMM) ? rho : 1.0;
   s->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
@@ -111,17 +119,17 @@ int bccb_batch_create(bccb_solver_t* out, const bccb_inst_t* insts, int n, const
       delete s;
       return fail(nullptr, BCCB_ERR_INVALID_ARG, "instance " + std::to_string(i) + ": bad M1/M2/offsets");
     }
-    if (!is_pow2(q.L1) || !is_pow2(q.L2) || q.L1 < 16 || q.L2 < 16 || q.L1 > 256 || q.L2 > 256) {
+    if (!is_pow2(q.L1) || !is_pow2(q.L2) || q.L1 < 16 || q.L2 < 16 || q.L1 > 1024 || q.L2 > 1024) {
       delete s;
       return fail(nullptr, BCCB_ERR_UNSUPPORTED,
-                  "instance " + std::to_string(i) + ": L1, L2 must be powers of two in [16, 256]");
+                  "instance " + std::to_string(i) + ": L1, L2 must be powers of two in [16, 1024]");
     }
     if (!(q.lam >= 0.0)) {
       delete s;
       return fail(nullptr, BCCB_ERR_INVALID_ARG, "instance " + std::to_string(i) + ": lam must be >= 0");
     }
-    const bccb::FusedEntry* fe = bccb::fused_lookup(q.L1, q.L2, algo == BCCB_ADMM);
-    if (!fe) {
+    const bool on_chip = prec == BCCB_F32 && q.L1 <= 256 && q.L2 <= 256;
+    if (on_chip && !bccb::fused_lookup(q.L1, q.L2, algo == BCCB_ADMM)) {
       delete s;
       return fail(nullptr, BCCB_ERR_UNSUPPORTED, "no fused kernel for this grid");
     }
@@ -165,10 +173,18 @@ int bccb_batch_create(bccb_solver_t* out, const bccb_inst_t* insts, int n, const
   for (auto& kv : by_shape) order.push_back({-(kv.first.first * kv.first.second), kv.first});
   std::sort(order.begin(), order.end());
   std::vector<int> ids;
+  bool any_mp = false;
   for (auto& o : order) {
     auto& v = by_shape[o.second];
     bccb::ShapeClass sc;
-    sc.entry = *bccb::fused_lookup(o.second.first, o.second.second, algo == BCCB_ADMM);
+    sc.L1 = o.second.first;
+    sc.L2 = o.second.second;
+    sc.multipass = !(prec == BCCB_F32 && sc.L1 <= 256 && sc.L2 <= 256);
+    if (!sc.multipass)
+      sc.entry = *bccb::fused_lookup(sc.L1, sc.L2, algo == BCCB_ADMM);
+    else
+      memset(&sc.entry, 0, sizeof(sc.entry));
+    any_mp = any_mp || sc.multipass;
     sc.first = (int)ids.size();
     sc.count = (int)v.size();
     ids.insert(ids.end(), v.begin(), v.end());
@@ -205,8 +221,20 @@ int bccb_batch_create(bccb_solver_t* out, const bccb_inst_t* insts, int n, const
   CREATE_CUDA(cudaMemcpy(s->d_mask_idx, mask_idx.data(), mask_idx.size() * sizeof(int), cudaMemcpyHostToDevice));
   CREATE_CUDA(cudaMemcpy(s->d_fused, fused.data(), n * sizeof(FusedInst), cudaMemcpyHostToDevice));
   CREATE_CUDA(cudaMemcpy(s->d_ids, ids.data(), n * sizeof(int), cudaMemcpyHostToDevice));
+  if (prec == BCCB_F64) {
+    CREATE_CUDA(dalloc(&s->d_mult64, s->total_L));
+    CREATE_CUDA(dalloc(&s->d_bt64, s->total_L));
+  }
+  if (any_mp) {
+    const size_t vb = prec == BCCB_F64 ? sizeof(double2) : sizeof(float2);
+    CREATE_CUDA(cudaMalloc(&s->d_mp_work, vb * (size_t)s->total_L));
+    CREATE_CUDA(cudaMalloc(&s->d_mp_s0, vb * (size_t)s->total_L));
+    CREATE_CUDA(cudaMalloc(&s->d_mp_s1, vb * (size_t)s->total_L));
+    CREATE_CUDA(bccb::prepare_multipass(s));
+  }
   CREATE_CUDA(bccb::fill_twiddles(s));
-  for (auto& c : s->classes) CREATE_CUDA(c.entry.prepare());
+  for (auto& c : s->classes)
+    if (!c.multipass) CREATE_CUDA(c.entry.prepare());
   if (s->classes.size() > 1) {
     CREATE_CUDA(cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming));
     for (size_t k = 0; k < s->classes.size(); ++k) {
@@ -233,7 +261,7 @@ int bccb_batch_solve(bccb_solver_t s, const void* y_dev, int iters, const void* 
   s->launches = 0;
   if (s->timing) BCCB_CUDA(s, cudaEventRecordWithFlags(s->ev[0], s->stream, cudaEventRecordExternal));
   if (s->algo == BCCB_FISTA) BCCB_CUDA(s, bccb::fista_schedule(s, iters));
-  const float2* y = reinterpret_cast<const float2*>(y_dev);
+  const void* y = y_dev;
   BCCB_CUDA(s, bccb::run_setup(s, y));
   if (s->timing) BCCB_CUDA(s, cudaEventRecordWithFlags(s->ev[1], s->stream, cudaEventRecordExternal));
   FusedArgs a{};
@@ -247,25 +275,28 @@ int bccb_batch_solve(bccb_solver_t s, const void* y_dev, int iters, const void* 
   a.aux_out = (s->algo == BCCB_ADMM) ? reinterpret_cast<float2*>(aux_out_dev) : nullptr;
   a.iters = iters;
   a.pad_ = 0;
-  if (s->classes.size() == 1) {
-    a.ids = s->d_ids;
-    BCCB_CUDA(s, s->classes[0].entry.launch(a, s->classes[0].count, s->stream));
+  auto launch_class = [&](const bccb::ShapeClass& c, cudaStream_t st) -> cudaError_t {
+    if (c.multipass)
+      return bccb::run_multipass(s, s->d_ids + c.first, c.count, iters, c0_dev, c_out_dev,
+                                 s->algo == BCCB_ADMM ? aux_out_dev : nullptr, st);
+    a.ids = s->d_ids + c.first;
     s->launches += 1;
+    return c.entry.launch(a, c.count, st);
+  };
+  if (s->classes.size() == 1) {
+    BCCB_CUDA(s, launch_class(s->classes[0], s->stream));
   } else {
     // one stream per shape class, forked from and joined back to the solver's stream
     BCCB_CUDA(s, cudaEventRecord(s->fork, s->stream));
     for (size_t k = 0; k < s->classes.size(); ++k) {
-      const auto& c = s->classes[k];
-      a.ids = s->d_ids + c.first;
       BCCB_CUDA(s, cudaStreamWaitEvent(s->class_streams[k], s->fork, 0));
-      BCCB_CUDA(s, c.entry.launch(a, c.count, s->class_streams[k]));
+      BCCB_CUDA(s, launch_class(s->classes[k], s->class_streams[k]));
       BCCB_CUDA(s, cudaEventRecord(s->class_done[k], s->class_streams[k]));
       BCCB_CUDA(s, cudaStreamWaitEvent(s->stream, s->class_done[k], 0));
-      s->launches += 1;
     }
   }
   if (s->timing) BCCB_CUDA(s, cudaEventRecordWithFlags(s->ev[2], s->stream, cudaEventRecordExternal));
-  if (check) BCCB_CUDA(s, bccb::run_check(s, y, reinterpret_cast<const float2*>(c_out_dev)));
+  if (check) BCCB_CUDA(s, bccb::run_check(s, y, c_out_dev));
   if (s->timing) BCCB_CUDA(s, cudaEventRecordWithFlags(s->ev[3], s->stream, cudaEventRecordExternal));
   s->last_checked = check != 0;
   return BCCB_OK;
@@ -275,14 +306,13 @@ int bccb_batch_solve_host(bccb_solver_t s, const void* y_host, int iters, void* 
   if (!s) return fail(nullptr, BCCB_ERR_INVALID_ARG, "solver is NULL");
   if (!y_host || !c_out_host) return fail(s, BCCB_ERR_INVALID_ARG, "y and c_out must be host pointers");
   BCCB_CUDA(s, cudaSetDevice(s->device));
-  if (!s->d_y_stage) BCCB_CUDA(s, dalloc(&s->d_y_stage, s->total_y));
-  if (!s->d_c_stage) BCCB_CUDA(s, dalloc(&s->d_c_stage, s->total_c));
-  BCCB_CUDA(s, cudaMemcpyAsync(s->d_y_stage, y_host, s->total_y * sizeof(float2), cudaMemcpyHostToDevice,
-                               s->stream));
+  const size_t vb = s->prec == BCCB_F64 ? sizeof(double2) : sizeof(float2);
+  if (!s->d_y_stage) BCCB_CUDA(s, dalloc(&s->d_y_stage, s->total_y * vb / sizeof(float2)));
+  if (!s->d_c_stage) BCCB_CUDA(s, dalloc(&s->d_c_stage, s->total_c * vb / sizeof(float2)));
+  BCCB_CUDA(s, cudaMemcpyAsync(s->d_y_stage, y_host, s->total_y * vb, cudaMemcpyHostToDevice, s->stream));
   int st = bccb_batch_solve(s, s->d_y_stage, iters, nullptr, s->d_c_stage, nullptr, check);
   if (st != BCCB_OK) return st;
-  BCCB_CUDA(s, cudaMemcpyAsync(c_out_host, s->d_c_stage, s->total_c * sizeof(float2), cudaMemcpyDeviceToHost,
-                               s->stream));
+  BCCB_CUDA(s, cudaMemcpyAsync(c_out_host, s->d_c_stage, s->total_c * vb, cudaMemcpyDeviceToHost, s->stream));
   BCCB_CUDA(s, cudaStreamSynchronize(s->stream));
   return BCCB_OK;
 }
@@ -435,12 +465,12 @@ int bccb_batch_tune(bccb_solver_t s, const void* y_dev, int probe_iters, const c
   const int admm = s->algo == BCCB_ADMM ? 1 : 0;
   bool need_probe = false;
   for (auto& c : s->classes)
-    if (!cached.count(std::make_tuple(c.entry.L1, c.entry.L2, admm))) need_probe = true;
+    if (!c.multipass && !cached.count(std::make_tuple(c.entry.L1, c.entry.L2, admm))) need_probe = true;
   FILE* out = nullptr;
   if (need_probe) {
     if (s->algo == BCCB_FISTA) BCCB_CUDA(s, bccb::fista_schedule(s, probe_iters));
     if (!s->d_probe) BCCB_CUDA(s, dalloc(&s->d_probe, s->total_c));
-    BCCB_CUDA(s, bccb::run_setup(s, reinterpret_cast<const float2*>(y_dev)));
+    BCCB_CUDA(s, bccb::run_setup(s, y_dev));
     if (cache_path) out = fopen(cache_path, "a");
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -450,6 +480,7 @@ int bccb_batch_tune(bccb_solver_t s, const void* y_dev, int probe_iters, const c
   }
   int status = BCCB_OK;
   for (auto& c : s->classes) {
+    if (c.multipass) continue;
     const auto key = std::make_tuple(c.entry.L1, c.entry.L2, admm);
     auto it = cached.find(key);
     if (it != cached.end()) {
@@ -508,12 +539,14 @@ int bccb_unrolled_fwd(bccb_solver_t s, const void* y_dev, int layers, const floa
   if (!s) return fail(nullptr, BCCB_ERR_INVALID_ARG, "solver is NULL");
   s->last_error.clear();
   if (s->algo != BCCB_FISTA) return fail(s, BCCB_ERR_INVALID_ARG, "the unrolled network needs a FISTA solver");
+  for (const auto& c : s->classes)
+    if (c.multipass) return fail(s, BCCB_ERR_UNSUPPORTED, "the unrolled network needs FP32 grids up to 256");
   if (!y_dev || !c_out_dev || !scale_dev || !thresh_dev || layers < 1)
     return fail(s, BCCB_ERR_INVALID_ARG, "bad y, c_out, scale, thresh or layers");
   BCCB_CUDA(s, cudaSetDevice(s->device));
   s->launches = 0;
   BCCB_CUDA(s, bccb::fista_schedule(s, layers));
-  const float2* y = reinterpret_cast<const float2*>(y_dev);
+  const void* y = y_dev;
   BCCB_CUDA(s, bccb::run_setup(s, y));
   FusedArgs a{};
   a.insts = s->d_fused;
@@ -532,7 +565,7 @@ int bccb_unrolled_fwd(bccb_solver_t s, const void* y_dev, int layers, const floa
     BCCB_CUDA(s, c.entry.launch(a, c.count, s->stream));
     s->launches += 1;
   }
-  if (check) BCCB_CUDA(s, bccb::run_check(s, y, reinterpret_cast<const float2*>(c_out_dev)));
+  if (check) BCCB_CUDA(s, bccb::run_check(s, y, c_out_dev));
   s->last_checked = check != 0;
   return BCCB_OK;
 }
@@ -573,7 +606,7 @@ int bccb_batch_tile(bccb_solver_t s, int L1, int L2, int* tile) {
   if (!s || !tile) return fail(s, BCCB_ERR_INVALID_ARG, "NULL argument");
   *tile = 0;
   for (const auto& c : s->classes)
-    if (c.entry.L1 == L1 && c.entry.L2 == L2) *tile = c.entry.tile;
+    if (c.L1 == L1 && c.L2 == L2) *tile = c.multipass ? 0 : c.entry.tile;
   return BCCB_OK;
 }
 

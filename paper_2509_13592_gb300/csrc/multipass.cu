@@ -1,0 +1,314 @@
+// Multi-pass ISTA / FISTA / ADMM solver for grids the fused on-chip kernel does not
+// hold (L_i up to 1024) and for the FP64 solve path.  Same iteration as the fused
+// kernel (Section III-B, eq:Rc with eq:ista / eq:fista / eq:admm):
+//     u = x - IFFT2(q . FFT2(x) - Bt)   (the identity part never enters the FFT)
+// but with the grid in global memory (L2-resident at 1024 x 1024 in FP32) and two
+// kernels per iteration:
+//   column pass: forward column DFTs, q . X - Bt, inverse column DFTs, for the
+//                Fourier columns p1 < kcols only (the spectrum vanishes beyond);
+//   row pass:    inverse row DFTs (columns >= kcols read as zero), the pointwise
+//                update of the state, and the next iteration's forward row DFTs.
+// V = float2 (complex64) or double2 (complex128); transforms are radix-4 Stockham
+// stages (one radix-2 stage for odd log2 n) staged in shared memory.
+#include "solver.h"
+
+namespace bccb {
+namespace {
+
+template <typename V>
+struct MpArgs {
+  const InstDesc* desc;
+  const int* ids;
+  const InstParams* par;
+  const FusedInst* fused;  // kcols
+  V* work;
+  V* s0;  // c (ISTA/FISTA) or z (ADMM)
+  V* s1;  // z (FISTA) or v (ADMM)
+  const typename ScalarOf<V>::T* mult;
+  const V* bt;
+  const V* tw;  // W_1024^e
+  const typename ScalarOf<V>::T* beta;
+  const V* c0;
+  V* c_out;
+  V* aux;
+  int algo;  // 0 ISTA, 1 FISTA, 2 ADMM
+  int it;
+  int last;
+  double rho;
+};
+
+// Stockham FFT of `cnt` interleaved sequences of length n (element e of sequence q at
+// x[e * cnt + q]), ping-pong between x and y; returns the buffer that holds the result.
+template <typename V, bool INV>
+__device__ V* fft_smem(V* x, V* y, int n, int cnt, const V* __restrict__ tw) {
+  int Ns = 1;
+  while (Ns * 4 <= n) {
+    const int q4 = n >> 2;
+    const int step = kTwiddleLen / (4 * Ns);
+    for (int idx = threadIdx.x; idx < q4 * cnt; idx += blockDim.x) {
+      const int q = idx % cnt, j = idx / cnt;
+      const int kk = j % Ns;
+      V v0 = x[j * cnt + q], v1 = x[(j + q4) * cnt + q], v2 = x[(j + 2 * q4) * cnt + q],
+        v3 = x[(j + 3 * q4) * cnt + q];
+      if (Ns > 1) {
+        v1 = twmul<INV>(v1, tw[kk * step]);
+        v2 = twmul<INV>(v2, tw[2 * kk * step]);
+        v3 = twmul<INV>(v3, tw[3 * kk * step]);
+      }
+      dft4<INV>(v0, v1, v2, v3);
+      const int o = (j / Ns) * 4 * Ns + kk;
+      y[o * cnt + q] = v0;
+      y[(o + Ns) * cnt + q] = v1;
+      y[(o + 2 * Ns) * cnt + q] = v2;
+      y[(o + 3 * Ns) * cnt + q] = v3;
+    }
+    __syncthreads();
+    V* t = x;
+    x = y;
+    y = t;
+    Ns *= 4;
+  }
+  if (Ns < n) {
+    const int h = n >> 1;
+    const int step = kTwiddleLen / (2 * Ns);
+    for (int idx = threadIdx.x; idx < h * cnt; idx += blockDim.x) {
+      const int q = idx % cnt, j = idx / cnt;
+      const int kk = j % Ns;
+      const V a = x[j * cnt + q];
+      const V b = twmul<INV>(x[(j + h) * cnt + q], tw[kk * step]);
+      const int o = (j / Ns) * 2 * Ns + kk;
+      y[o * cnt + q] = cadd(a, b);
+      y[(o + Ns) * cnt + q] = csub(a, b);
+    }
+    __syncthreads();
+    x = y;
+  }
+  return x;
+}
+
+template <typename V>
+__device__ __forceinline__ V shrink(V u, typename ScalarOf<V>::T kappa) {
+  using T = typename ScalarOf<V>::T;
+  const T r2 = u.x * u.x + u.y * u.y;
+  if (r2 > kappa * kappa) {
+    const T s = (T)1 - kappa / sqrt(r2);
+    return cmk<V>(u.x * s, u.y * s);
+  }
+  return cmk<V>((T)0, (T)0);
+}
+
+__device__ __forceinline__ int active_cols(int kcols, int L1) { return min(L1, (kcols + 3) & ~3); }
+
+// state <- warm start (or zero); work row input of the first forward row pass is built there too
+template <typename V>
+__global__ void mp_init_kernel(MpArgs<V> a) {
+  using T = typename ScalarOf<V>::T;
+  const int inst = a.ids[blockIdx.x];
+  const InstDesc d = a.desc[inst];
+  const int L = d.L1 * d.L2;
+  for (int cell = blockIdx.y * blockDim.x + threadIdx.x; cell < L; cell += gridDim.y * blockDim.x) {
+    const V x = a.c0 ? a.c0[d.c_off + cell] : cmk<V>((T)0, (T)0);
+    a.s0[d.g_off + cell] = x;
+    a.s1[d.g_off + cell] = (a.algo == 2) ? cmk<V>((T)0, (T)0) : x;
+  }
+}
+
+// MODE 0: forward row DFTs of the initial input; 1: inverse row DFTs, update, forward row
+// DFTs of the next input; 2: inverse row DFTs and update (last iteration)
+template <typename V, int MODE>
+__global__ void mp_rows_kernel(MpArgs<V> a) {
+  using T = typename ScalarOf<V>::T;
+  const int inst = a.ids[blockIdx.x];
+  const InstDesc d = a.desc[inst];
+  const int row = blockIdx.y;
+  if (row >= d.L2) return;
+  const int L1 = d.L1;
+  const int kc = active_cols(a.fused[inst].kcols, L1);
+  extern __shared__ unsigned char mp_sm[];
+  V* x = reinterpret_cast<V*>(mp_sm);
+  V* y = x + L1;
+  V* work = a.work + d.g_off + (int64_t)row * L1;
+  V* s0 = a.s0 + d.g_off + (int64_t)row * L1;
+  V* s1 = a.s1 + d.g_off + (int64_t)row * L1;
+  V* res = x;
+  if (MODE == 0) {
+    for (int e = threadIdx.x; e < L1; e += blockDim.x)
+      x[e] = (a.algo == 2) ? csub(s0[e], s1[e]) : (a.algo == 1 ? s1[e] : s0[e]);
+    __syncthreads();
+  } else {
+    for (int e = threadIdx.x; e < L1; e += blockDim.x) x[e] = (e < kc) ? work[e] : cmk<V>((T)0, (T)0);
+    __syncthreads();
+    res = fft_smem<V, true>(x, y, L1, 1, a.tw);
+    const InstParams p = a.par[inst];
+    const T kappa = (T)(a.algo == 2 ? p.lam / a.rho : p.mu * p.lam);
+    const T beta = (a.algo == 1) ? a.beta[a.it] : (T)0;
+    V* aux = a.aux ? a.aux + d.c_off + (int64_t)row * L1 : nullptr;
+    for (int e = threadIdx.x; e < L1; e += blockDim.x) {
+      const V g = res[e];
+      V next;
+      if (a.algo != 2) {
+        const V c_old = s0[e];
+        const V xin = (a.algo == 1) ? s1[e] : c_old;
+        const V cn = shrink(csub(xin, g), kappa);
+        s0[e] = cn;
+        if (a.algo == 1) {
+          next = cadd(cn, cscale(csub(cn, c_old), beta));
+          s1[e] = next;
+        } else {
+          next = cn;
+        }
+      } else {
+        const V zo = s0[e], vo = s1[e];
+        const V un = csub(zo, g);  // c^(t+1) + v^(t)
+        const V zn = shrink(un, kappa);
+        const V vn = csub(un, zn);
+        s0[e] = zn;
+        s1[e] = vn;
+        next = csub(zn, vn);
+        if (MODE == 2 && aux) aux[e] = csub(un, vo);
+      }
+      res[e] = next;
+    }
+    __syncthreads();
+  }
+  if (MODE != 2) {
+    V* other = (res == x) ? y : x;
+    V* out = fft_smem<V, false>(res, other, L1, 1, a.tw);
+    for (int e = threadIdx.x; e < kc; e += blockDim.x) work[e] = out[e];
+  }
+}
+
+// columns c0 .. c0 + cnt - 1 (< kcols): forward DFT over the column, q . X - Bt, inverse DFT
+template <typename V>
+__global__ void mp_cols_kernel(MpArgs<V> a, int cpb) {
+  const int inst = a.ids[blockIdx.x];
+  const InstDesc d = a.desc[inst];
+  const int kc = active_cols(a.fused[inst].kcols, d.L1);
+  const int c0 = blockIdx.y * cpb;
+  if (c0 >= kc) return;
+  const int cnt = min(cpb, kc - c0);
+  extern __shared__ unsigned char mp_sm[];
+  V* x = reinterpret_cast<V*>(mp_sm);
+  V* y = x + d.L2 * cpb;
+  V* work = a.work + d.g_off;
+  for (int idx = threadIdx.x; idx < d.L2 * cnt; idx += blockDim.x) {
+    const int e = idx / cnt, q = idx % cnt;
+    x[idx] = work[(int64_t)e * d.L1 + c0 + q];
+  }
+  __syncthreads();
+  V* r = fft_smem<V, false>(x, y, d.L2, cnt, a.tw);
+  for (int idx = threadIdx.x; idx < d.L2 * cnt; idx += blockDim.x) {
+    const int e = idx / cnt, q = idx % cnt;
+    const int64_t f = d.g_off + (int64_t)e * d.L1 + c0 + q;
+    const auto m = a.mult[f];
+    const V b = a.bt[f];
+    const V v = r[idx];
+    r[idx] = cmk<V>(v.x * m - b.x, v.y * m - b.y);
+  }
+  __syncthreads();
+  V* other = (r == x) ? y : x;
+  V* out = fft_smem<V, true>(r, other, d.L2, cnt, a.tw);
+  for (int idx = threadIdx.x; idx < d.L2 * cnt; idx += blockDim.x) {
+    const int e = idx / cnt, q = idx % cnt;
+    work[(int64_t)e * d.L1 + c0 + q] = out[idx];
+  }
+}
+
+template <typename V>
+__global__ void mp_output_kernel(MpArgs<V> a) {
+  const int inst = a.ids[blockIdx.x];
+  const InstDesc d = a.desc[inst];
+  const int L = d.L1 * d.L2;
+  for (int cell = blockIdx.y * blockDim.x + threadIdx.x; cell < L; cell += gridDim.y * blockDim.x)
+    a.c_out[d.c_off + cell] = a.s0[d.g_off + cell];
+}
+
+constexpr int kMpThreads = 256;
+
+int mp_cols_per_block(int max_L2, int vbytes) {
+  // two L2 x cpb tiles within 96 KB
+  int cpb = 16;
+  while (cpb > 1 && 2 * max_L2 * cpb * vbytes > 96 * 1024) cpb >>= 1;
+  return cpb;
+}
+
+template <typename V>
+cudaError_t run_t(bccb_solver* s, const int* ids, int count, int iters, const void* c0, void* c_out, void* aux,
+                  cudaStream_t st) {
+  using T = typename ScalarOf<V>::T;
+  MpArgs<V> a{};
+  a.desc = s->d_desc;
+  a.ids = ids;
+  a.par = s->d_par;
+  a.fused = s->d_fused;
+  a.work = static_cast<V*>(s->d_mp_work);
+  a.s0 = static_cast<V*>(s->d_mp_s0);
+  a.s1 = static_cast<V*>(s->d_mp_s1);
+  if constexpr (sizeof(T) == 8) {
+    a.mult = s->d_mult64;
+    a.bt = s->d_bt64;
+    a.tw = s->d_tw64;
+    a.beta = s->d_beta64;
+  } else {
+    a.mult = s->d_mult;
+    a.bt = s->d_cterm;
+    a.tw = s->d_tw32;
+    a.beta = s->d_beta;
+  }
+  a.c0 = static_cast<const V*>(c0);
+  a.c_out = static_cast<V*>(c_out);
+  a.aux = static_cast<V*>(aux);
+  a.algo = s->algo;
+  a.rho = s->rho;
+  const int cells = s->max_L1 * s->max_L2;
+  const dim3 gcell((unsigned)count, (unsigned)min(64, (cells + kMpThreads - 1) / kMpThreads));
+  const dim3 grow((unsigned)count, (unsigned)s->max_L2);
+  const int cpb = mp_cols_per_block(s->max_L2, (int)sizeof(V));
+  const dim3 gcol((unsigned)count, (unsigned)((s->max_L1 + cpb - 1) / cpb));
+  const size_t sm_row = 2 * (size_t)s->max_L1 * sizeof(V);
+  const size_t sm_col = 2 * (size_t)s->max_L2 * cpb * sizeof(V);
+  mp_init_kernel<V><<<gcell, kMpThreads, 0, st>>>(a);
+  mp_rows_kernel<V, 0><<<grow, kMpThreads, sm_row, st>>>(a);
+  s->launches += 2;
+  for (int it = 0; it < iters; ++it) {
+    a.it = it;
+    mp_cols_kernel<V><<<gcol, kMpThreads, sm_col, st>>>(a, cpb);
+    if (it + 1 < iters)
+      mp_rows_kernel<V, 1><<<grow, kMpThreads, sm_row, st>>>(a);
+    else
+      mp_rows_kernel<V, 2><<<grow, kMpThreads, sm_row, st>>>(a);
+    s->launches += 2;
+  }
+  mp_output_kernel<V><<<gcell, kMpThreads, 0, st>>>(a);
+  s->launches += 1;
+  return cudaGetLastError();
+}
+
+template <typename V>
+cudaError_t prepare_t(int max_L1, int max_L2) {
+  const int cpb = mp_cols_per_block(max_L2, (int)sizeof(V));
+  const int sm_col = 2 * max_L2 * cpb * (int)sizeof(V);
+  const int sm_row = 2 * max_L1 * (int)sizeof(V);
+  cudaError_t e = cudaFuncSetAttribute(mp_cols_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_col);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(mp_rows_kernel<V, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_row);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(mp_rows_kernel<V, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_row);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(mp_rows_kernel<V, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_row);
+  return e;
+}
+
+}  // namespace
+
+cudaError_t prepare_multipass(bccb_solver* s) {
+  return s->prec == 1 ? prepare_t<double2>(s->max_L1, s->max_L2) : prepare_t<float2>(s->max_L1, s->max_L2);
+}
+
+cudaError_t run_multipass(bccb_solver* s, const int* ids, int count, int iters, const void* c0, void* c_out,
+                          void* aux, cudaStream_t stream) {
+  if (s->prec == 1) return run_t<double2>(s, ids, count, iters, c0, c_out, aux, stream);
+  return run_t<float2>(s, ids, count, iters, c0, c_out, aux, stream);
+}
+
+}  // namespace bccb

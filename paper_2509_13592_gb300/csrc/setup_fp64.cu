@@ -63,15 +63,16 @@ __global__ void fft64_rows_kernel(const InstDesc* __restrict__ desc, double2* ba
   for (int e = threadIdx.x; e < d.L1; e += blockDim.x) g[e] = out[e];
 }
 
-constexpr int kColsPerBlock = 8;
+// columns staged per block: 8, or fewer so that two L2 x cpb FP64 tiles fit in 128 KB
+int cols_per_block(int max_L2) { return max_L2 <= 512 ? 8 : 4096 / max_L2; }
 
-// In-place DFT of every column (length L2) of every instance's grid, kColsPerBlock at a time.
+// In-place DFT of every column (length L2) of every instance's grid, cpb at a time.
 __global__ void fft64_cols_kernel(const InstDesc* __restrict__ desc, double2* base, int inv,
-                                  const double2* __restrict__ tw) {
+                                  const double2* __restrict__ tw, int cpb) {
   const InstDesc d = desc[blockIdx.x];
-  const int c0 = blockIdx.y * kColsPerBlock;
+  const int c0 = blockIdx.y * cpb;
   if (c0 >= d.L1) return;
-  const int cnt = min(kColsPerBlock, d.L1 - c0);
+  const int cnt = min(cpb, d.L1 - c0);
   extern __shared__ double2 sm64[];
   double2* x = sm64;
   double2* y = sm64 + d.L2 * cnt;
@@ -88,13 +89,14 @@ __global__ void fft64_cols_kernel(const InstDesc* __restrict__ desc, double2* ba
   }
 }
 
-// count grid (for Lambda) and the signed measurement grid (for b)
+// count grid (for Lambda) and the signed measurement grid (for b); Y = float2 or double2
+template <typename Y>
 __global__ void scatter_kernel(const InstDesc* __restrict__ desc, const int* __restrict__ mask_idx,
-                               const float2* __restrict__ y, double2* cnt_grid, double2* meas_grid) {
+                               const Y* __restrict__ y, double2* cnt_grid, double2* meas_grid) {
   const InstDesc d = desc[blockIdx.x];
   const int L = d.L1 * d.L2;
   const int* mi = mask_idx + d.mask_off;
-  const float2* yi = y + d.y_off;
+  const Y* yi = y + d.y_off;
   for (int cell = blockIdx.y * blockDim.x + threadIdx.x; cell < L; cell += gridDim.y * blockDim.x) {
     const int p1 = cell % d.L1, p2 = cell / d.L1;
     double cnt = 0.0;
@@ -150,7 +152,7 @@ struct SumOp {
 // round-off of the FP64 DFTs of an exactly zero eigenvalue and are set to 0.
 __global__ void eig_mult_kernel(const InstDesc* __restrict__ desc, const double2* __restrict__ lam_c,
                                 const double2* __restrict__ sgrid, double* lam64, InstParams* par, float* mult,
-                                float2* bt, FusedInst* fused, int algo, double rho) {
+                                float2* bt, double* mult64, double2* bt64, FusedInst* fused, int algo, double rho) {
   __shared__ double sh[32];
   const InstDesc d = desc[blockIdx.x];
   const int L = d.L1 * d.L2;
@@ -177,7 +179,11 @@ __global__ void eig_mult_kernel(const InstDesc* __restrict__ desc, const double2
     const float2 bf = make_float2((float)(sv.x * bs), (float)(sv.y * bs));
     mult[d.g_off + cell] = mf;
     bt[d.g_off + cell] = bf;
-    if (mf != 0.f || bf.x != 0.f || bf.y != 0.f) kc = fmax(kc, (double)(cell % d.L1 + 1));
+    if (mult64) {
+      mult64[d.g_off + cell] = m;
+      bt64[d.g_off + cell] = make_double2(sv.x * bs, sv.y * bs);
+    }
+    if (m != 0.0 || sv.x != 0.0 || sv.y != 0.0) kc = fmax(kc, (double)(cell % d.L1 + 1));
   }
   kc = block_reduce(kc, MaxOp(), sh, 0.0);
   if (threadIdx.x == 0) {
@@ -208,25 +214,25 @@ __global__ void lam_kappa_kernel(const InstDesc* __restrict__ desc, const double
   }
 }
 
-// w <- c (FP32 solution, solver grid layout)
-__global__ void load_solution_kernel(const InstDesc* __restrict__ desc, const float2* __restrict__ c,
-                                     double2* w) {
+// w <- c (solution in the solver's grid layout; C = float2 or double2)
+template <typename C>
+__global__ void load_solution_kernel(const InstDesc* __restrict__ desc, const C* __restrict__ c, double2* w) {
   const InstDesc d = desc[blockIdx.x];
   const int L = d.L1 * d.L2;
   for (int cell = blockIdx.y * blockDim.x + threadIdx.x; cell < L; cell += gridDim.y * blockDim.x) {
-    const float2 v = c[d.c_off + cell];
+    const C v = c[d.c_off + cell];
     w[d.g_off + cell] = make_double2((double)v.x, (double)v.y);
   }
 }
 
 // sum_n |y_n - (A c)_n|^2 with (A c)_n = (-1)^(m1+m2) FFT2(c)[m2 mod L2, m1 mod L1]
+template <typename Y>
 __global__ void data_residual_kernel(const InstDesc* __restrict__ desc, const int* __restrict__ mask_idx,
-                                     const float2* __restrict__ y, const double2* __restrict__ cf,
-                                     double* red) {
+                                     const Y* __restrict__ y, const double2* __restrict__ cf, double* red) {
   __shared__ double sh[32];
   const InstDesc d = desc[blockIdx.x];
   const int* mi = mask_idx + d.mask_off;
-  const float2* yi = y + d.y_off;
+  const Y* yi = y + d.y_off;
   double acc = 0.0;
   for (int pos = threadIdx.x; pos < d.M1 * d.M2; pos += blockDim.x) {
     const int n = mi[pos];
@@ -253,8 +259,9 @@ __global__ void mul_lambda_kernel(const InstDesc* __restrict__ desc, const doubl
 }
 
 // r = b - G c (G c = IFFT2(Lambda FFT2(c)), held unnormalised in w); KKT residual and objective
+template <typename C>
 __global__ void kkt_final_kernel(const InstDesc* __restrict__ desc, const double2* __restrict__ b64,
-                                 const double2* __restrict__ gc, const float2* __restrict__ c,
+                                 const double2* __restrict__ gc, const C* __restrict__ c,
                                  const InstParams* __restrict__ par, const double* __restrict__ red,
                                  double* kkt, double* obj) {
   __shared__ double sh[32];
@@ -267,7 +274,7 @@ __global__ void kkt_final_kernel(const InstDesc* __restrict__ desc, const double
     const double2 bv = b64[d.g_off + cell];
     const double2 gv = gc[d.g_off + cell];
     const double rx = bv.x - gv.x * inv_L, ry = bv.y - gv.y * inv_L;
-    const float2 cv = c[d.c_off + cell];
+    const C cv = c[d.c_off + cell];
     const double cx = cv.x, cy = cv.y;
     const double mag = sqrt(cx * cx + cy * cy);
     double viol;
@@ -288,14 +295,16 @@ __global__ void kkt_final_kernel(const InstDesc* __restrict__ desc, const double
   }
 }
 
-__global__ void fista_beta_kernel(float* beta, int iters) {
+__global__ void fista_beta_kernel(float* beta, double* beta64, int iters) {
   // alpha_1 = 1, alpha_(t+1) = (1 + sqrt(1 + 4 alpha_t^2))/2, beta_t = (alpha_t - 1)/alpha_(t+1),
   // evaluated in FP64 with explicit round-to-nearest operations (no contraction).
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double a = 1.0;
   for (int t = 0; t < iters; ++t) {
     const double an = __dmul_rn(__dadd_rn(1.0, __dsqrt_rn(__dadd_rn(1.0, __dmul_rn(__dmul_rn(4.0, a), a)))), 0.5);
-    beta[t] = (float)__ddiv_rn(__dadd_rn(a, -1.0), an);
+    const double b = __ddiv_rn(__dadd_rn(a, -1.0), an);
+    beta[t] = (float)b;
+    if (beta64) beta64[t] = b;
     a = an;
   }
 }
@@ -310,17 +319,18 @@ cudaError_t fft2_64(bccb_solver* s, double2* grid, int inv) {
   s->launches += 2;
   const size_t smr = (size_t)2 * s->max_L1 * sizeof(double2);
   fft64_rows_kernel<<<dim3(s->n, s->max_L2), 128, smr, s->stream>>>(s->d_desc, grid, inv, s->d_tw64);
-  const size_t smc = (size_t)2 * s->max_L2 * kColsPerBlock * sizeof(double2);
-  fft64_cols_kernel<<<dim3(s->n, (s->max_L1 + kColsPerBlock - 1) / kColsPerBlock), 128, smc, s->stream>>>(
-      s->d_desc, grid, inv, s->d_tw64);
+  const int cpb = cols_per_block(s->max_L2);
+  const size_t smc = (size_t)2 * s->max_L2 * cpb * sizeof(double2);
+  fft64_cols_kernel<<<dim3(s->n, (s->max_L1 + cpb - 1) / cpb), 128, smc, s->stream>>>(s->d_desc, grid, inv,
+                                                                                        s->d_tw64, cpb);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t fill_twiddles(bccb_solver* s) {
-  // the column pass stages kColsPerBlock columns of length L2 twice (ping-pong)
-  const int col_smem = 2 * s->max_L2 * kColsPerBlock * (int)sizeof(double2);
+  // the column pass stages cpb columns of length L2 twice (ping-pong)
+  const int col_smem = 2 * s->max_L2 * cols_per_block(s->max_L2) * (int)sizeof(double2);
   cudaError_t e0 = cudaFuncSetAttribute(fft64_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem);
   if (e0 != cudaSuccess) return e0;
   std::vector<float2> t32(kTwiddleLen);
@@ -339,48 +349,64 @@ cudaError_t fista_schedule(bccb_solver* s, int iters) {
   if (iters <= 0 || s->beta_len == iters) return cudaSuccess;
   if (iters > s->beta_cap) {
     if (s->d_beta) cudaFree(s->d_beta);
+    if (s->d_beta64) cudaFree(s->d_beta64);
     s->d_beta = nullptr;
+    s->d_beta64 = nullptr;
     cudaError_t err = cudaMalloc(&s->d_beta, (size_t)iters * sizeof(float));
+    if (err == cudaSuccess && s->prec == 1) err = cudaMalloc(&s->d_beta64, (size_t)iters * sizeof(double));
     if (err != cudaSuccess) return err;
     s->beta_cap = iters;
   }
-  fista_beta_kernel<<<1, 32, 0, s->stream>>>(s->d_beta, iters);
+  fista_beta_kernel<<<1, 32, 0, s->stream>>>(s->d_beta, s->d_beta64, iters);
   s->launches += 1;
   s->beta_len = iters;
   return cudaGetLastError();
 }
 
-cudaError_t run_setup(bccb_solver* s, const float2* y_dev) {
+cudaError_t run_setup(bccb_solver* s, const void* y_dev) {
   const dim3 gc = grid_cells(s);
   // count grid -> d_w64, signed measurement grid s -> d_b64
-  scatter_kernel<<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_mask_idx, y_dev, s->d_w64, s->d_b64);
+  if (s->prec == 1)
+    scatter_kernel<double2><<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_mask_idx,
+                                                             static_cast<const double2*>(y_dev), s->d_w64, s->d_b64);
+  else
+    scatter_kernel<float2><<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_mask_idx,
+                                                           static_cast<const float2*>(y_dev), s->d_w64, s->d_b64);
   s->launches += 3;  // scatter, eig_mult, lam_kappa
   cudaError_t err;
   if ((err = fft2_64(s, s->d_w64, 1)) != cudaSuccess) return err;  // first column of the Gram
   if ((err = fft2_64(s, s->d_w64, 0)) != cudaSuccess) return err;  // Lambda (eq:lambda)
   eig_mult_kernel<<<s->n, kThreads, 0, s->stream>>>(s->d_desc, s->d_w64, s->d_b64, s->d_lam64, s->d_par,
-                                                     s->d_mult, s->d_cterm, s->d_fused, s->algo, s->rho);
+                                                     s->d_mult, s->d_cterm, s->d_mult64, s->d_bt64, s->d_fused,
+                                                     s->algo, s->rho);
   if ((err = fft2_64(s, s->d_b64, 1)) != cudaSuccess) return err;  // b = A^H y
   lam_kappa_kernel<<<s->n, kThreads, 0, s->stream>>>(s->d_desc, s->d_b64, s->d_par, s->d_fused, s->algo, s->rho);
   return cudaGetLastError();
 }
 
-cudaError_t run_check(bccb_solver* s, const float2* y_dev, const float2* c_dev) {
+template <typename V>
+cudaError_t run_check_t(bccb_solver* s, const V* y_dev, const V* c_dev) {
   const dim3 gc = grid_cells(s);
-  load_solution_kernel<<<gc, kThreads, 0, s->stream>>>(s->d_desc, c_dev, s->d_w64);
+  load_solution_kernel<V><<<gc, kThreads, 0, s->stream>>>(s->d_desc, c_dev, s->d_w64);
   s->launches += 4;  // load_solution, data_residual, mul_lambda, kkt_final
   cudaError_t err;
   if ((err = fft2_64(s, s->d_w64, 0)) != cudaSuccess) return err;
-  data_residual_kernel<<<s->n, kThreads, 0, s->stream>>>(s->d_desc, s->d_mask_idx, y_dev, s->d_w64, s->d_red);
+  data_residual_kernel<V><<<s->n, kThreads, 0, s->stream>>>(s->d_desc, s->d_mask_idx, y_dev, s->d_w64, s->d_red);
   mul_lambda_kernel<<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_lam64, s->d_w64);
   if ((err = fft2_64(s, s->d_w64, 1)) != cudaSuccess) return err;
-  kkt_final_kernel<<<s->n, kThreads, 0, s->stream>>>(s->d_desc, s->d_b64, s->d_w64, c_dev, s->d_par, s->d_red,
-                                                      s->d_kkt, s->d_obj);
+  kkt_final_kernel<V><<<s->n, kThreads, 0, s->stream>>>(s->d_desc, s->d_b64, s->d_w64, c_dev, s->d_par, s->d_red,
+                                                         s->d_kkt, s->d_obj);
   return cudaGetLastError();
 }
 
+cudaError_t run_check(bccb_solver* s, const void* y_dev, const void* c_dev) {
+  if (s->prec == 1)
+    return run_check_t<double2>(s, static_cast<const double2*>(y_dev), static_cast<const double2*>(c_dev));
+  return run_check_t<float2>(s, static_cast<const float2*>(y_dev), static_cast<const float2*>(c_dev));
+}
+
 cudaError_t prepare_fp64_passes(int max_L2) {
-  const int col_smem = 2 * max_L2 * kColsPerBlock * (int)sizeof(double2);
+  const int col_smem = 2 * max_L2 * cols_per_block(max_L2) * (int)sizeof(double2);
   return cudaFuncSetAttribute(fft64_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem);
 }
 

@@ -31,7 +31,9 @@ struct InstParams {
 };
 
 struct ShapeClass {
-  FusedEntry entry;
+  FusedEntry entry;  // fused kernel (multipass == 0)
+  int multipass;     // 1: the multi-pass solver (grids above 256 or the FP64 path)
+  int L1, L2;
   int first;  // offset into the class-sorted id list
   int count;
 };
@@ -41,7 +43,7 @@ struct ShapeClass {
 struct bccb_solver {
   int n = 0;
   int algo = 1;
-  int prec = 0;
+  int prec = 0;  // 0: complex64 path, 1: complex128 (FP64 check path)
   double rho = 1.0;
   cudaStream_t stream = nullptr;
   int device = 0;
@@ -64,6 +66,7 @@ struct bccb_solver {
   bccb::FusedInst* d_fused = nullptr;
   int* d_ids = nullptr;
   float* d_beta = nullptr;
+  double* d_beta64 = nullptr;
   int beta_cap = 0;
   int beta_len = -1;
   double* d_kkt = nullptr;
@@ -88,17 +91,27 @@ struct bccb_solver {
   cudaGraphExec_t graph = nullptr;
   // probe output for the autotuner
   float2* d_probe = nullptr;
+  // multi-pass solver: FP64 multiplier and constant term, state grids (complex64 or complex128)
+  double* d_mult64 = nullptr;
+  double2* d_bt64 = nullptr;
+  void* d_mp_work = nullptr;
+  void* d_mp_s0 = nullptr;
+  void* d_mp_s1 = nullptr;
 };
 
 namespace bccb {
 // setup_fp64.cu
 // each returns the CUDA status and adds its kernel launches to s->launches
-cudaError_t run_setup(bccb_solver* s, const float2* y_dev);
-cudaError_t run_check(bccb_solver* s, const float2* y_dev, const float2* c_dev);
+cudaError_t run_setup(bccb_solver* s, const void* y_dev);
+cudaError_t run_check(bccb_solver* s, const void* y_dev, const void* c_dev);
 cudaError_t fill_twiddles(bccb_solver* s);
 cudaError_t fista_schedule(bccb_solver* s, int iters);
 // shared-memory opt-in of the FP64 column pass for grids with up to max_L2 rows
 cudaError_t prepare_fp64_passes(int max_L2);
+// multipass.cu: all iterations of one multi-pass class (ids[0..count)) on `stream`
+cudaError_t prepare_multipass(bccb_solver* s);
+cudaError_t run_multipass(bccb_solver* s, const int* ids, int count, int iters, const void* c0, void* c_out,
+                          void* aux, cudaStream_t stream);
 // fused_inst.cu / fused_dispatch.cu: tile 0 = the default 8192-element tile
 const FusedEntry* fused_lookup(int L1, int L2, bool admm, int tile = 0);
 const AdjointEntry* adjoint_lookup(int L1, int L2);

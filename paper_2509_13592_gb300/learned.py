@@ -199,3 +199,81 @@ def train(cfg: TrainConfig, resume: bool = False, log=print):
                        cfg.checkpoint)
     net.close()
     return log_a.detach().exp(), log_t.detach().exp(), history
+
+
+def evaluate(cfg: TrainConfig, scale, thresh, n_eval=8192, first=10**7, sweep=(16, 32, 64, 128, 256, 512),
+             kkt_tol=1e-2):
+    """Batched inference on n_eval held-out snapshots: the network's time and relative error against
+    target_iters-iteration plain FISTA, plain FISTA's error and time at the iteration counts in `sweep`,
+    and how many snapshots the KKT check sends to the fallback."""
+    mask = fixed_mask(cfg)
+    y = snapshot_batch(cfg, mask, first, n_eval)
+    L = cfg.L1 * cfg.L2
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        ev[0].record()
+        out = fn()
+        ev[1].record()
+        torch.cuda.synchronize()
+        return out, ev[0].elapsed_time(ev[1])
+
+    inst = dict(M1=cfg.M1, M2=cfg.M2, L1=cfg.L1, L2=cfg.L2, mask=mask, y=np.zeros(cfg.N, np.complex64),
+                lam=cfg.lam_frac, lam_is_frac=True)
+    solver = B.BatchSolver([inst] * n_eval, "fista")
+    out = torch.empty(n_eval * L, dtype=torch.complex64, device="cuda")
+    solver.solve(y, 10, out, check=False)  # warm-up (setup, momentum table)
+
+    def plain(iters):
+        o = torch.empty(n_eval * L, dtype=torch.complex64, device="cuda")
+        solver.solve(y, iters, o, check=False)
+        return o
+
+    ref, t_ref = timed(lambda: plain(cfg.target_iters))
+    net = UnrolledNet(cfg.M1, cfg.M2, mask, cfg.L1, cfg.L2, n_eval, cfg.lam_frac)
+    with torch.no_grad():
+        net_forward(net, y, scale, thresh)  # warm-up
+        c_net, t_net = timed(lambda: net_forward(net, y, scale, thresh))
+    res = {"n_eval": n_eval, "layers": int(scale.numel()), "target_iters": cfg.target_iters,
+           "target_ms": t_ref, "net_ms": t_net,
+           "net_rel_err_mean": relative_errors(c_net, ref, n_eval, L).mean().item(),
+           "net_rel_err_median": relative_errors(c_net, ref, n_eval, L).median().item(), "plain": {}}
+    for it in sweep:
+        o, t = timed(lambda: plain(it))
+        e = relative_errors(o, ref, n_eval, L)
+        res["plain"][it] = {"ms": t, "rel_err_mean": e.mean().item(), "rel_err_median": e.median().item()}
+    _, kkt, fb = infer_with_fallback(net, y, scale, thresh, kkt_tol=kkt_tol, fallback_iters=1)
+    res["kkt_tol"] = kkt_tol
+    res["kkt_fail_fraction"] = float(fb.mean())
+    res["kkt_median"] = float(np.median(kkt))
+    net.close()
+    solver.close()
+    return res
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser(description="train and evaluate the unrolled FISTA network")
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--layers", type=int, default=16)
+    ap.add_argument("--lr", type=float, default=0.05)
+    ap.add_argument("--eval", type=int, default=8192)
+    ap.add_argument("--checkpoint", default=None)
+    ap.add_argument("--resume", action="store_true")
+    args = ap.parse_args()
+    cfg = TrainConfig(layers=args.layers, batch=args.batch, steps=args.steps, lr=args.lr,
+                      checkpoint=args.checkpoint)
+    import time
+
+    t0 = time.time()
+    a, t, hist = train(cfg, resume=args.resume, log=lambda m: print(m, flush=True))
+    train_s = time.time() - t0
+    res = evaluate(cfg, a, t, n_eval=args.eval)
+    res.update({"train_steps": args.steps, "train_batch": args.batch, "train_snapshots": args.steps * args.batch,
+                "train_seconds": train_s, "loss_first": hist[0] if hist else None,
+                "loss_last": hist[-1] if hist else None, "scale": a.tolist(), "thresh": t.tolist()})
+    print(json.dumps(res), flush=True)

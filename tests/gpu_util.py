@@ -30,14 +30,15 @@ def oracle_run(s, algo, iters, lam=None, rho=1.0, A=None):
     return dict(c=c, u=u, kappa=kappa, A=A, lam=lam, aux=aux)
 
 
-def gpu_run(lib, snaps, lams, algo, iters, rho=1.0, check=True, c0=None):
+def gpu_run(lib, snaps, lams, algo, iters, rho=1.0, check=True, c0=None, prec="f32"):
     import torch
 
-    solver = lib.BatchSolver([inst(s, l) for s, l in zip(snaps, lams)], algo, rho)
+    solver = lib.BatchSolver([inst(s, l) for s, l in zip(snaps, lams)], algo, rho, prec=prec)
+    cdt = torch.complex128 if prec == "f64" else torch.complex64
     y = torch.from_numpy(solver.y_host).cuda()
-    c = torch.zeros(solver.total_c, dtype=torch.complex64, device="cuda")
+    c = torch.zeros(solver.total_c, dtype=cdt, device="cuda")
     aux = torch.zeros_like(c) if algo == "admm" else None
-    c0_t = None if c0 is None else torch.from_numpy(np.asarray(c0, np.complex64)).cuda()
+    c0_t = None if c0 is None else torch.from_numpy(np.asarray(c0, solver.dtype)).cuda()
     solver.solve(y, iters, c, c0=c0_t, aux_out=aux, check=check)
     torch.cuda.synchronize()
     res = solver.results() if check else None

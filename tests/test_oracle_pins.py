@@ -377,3 +377,13 @@ def test_unrolled_backward_matches_finite_differences():
         e[k] = h
         fd = (loss(mu, th + e) - loss(mu, th - e)) / (2 * h)
         assert abs(fd - d_th[k]) <= 1e-5 * max(1.0, abs(fd)), (k, fd, d_th[k])
+
+
+def test_column_and_kronecker_helpers_match_dense_dictionary():
+    """The large-grid helpers (selected columns, b from the Kronecker factors) equal the dense
+    construction on grids where both fit."""
+    s, A = _small_problem(seed=13, M1=6, M2=5, N=17, L1=16, L2=32)
+    cols = np.array([0, 1, 31, 200, 511])
+    np.testing.assert_allclose(oracle.dictionary_columns(s.mask, 6, 5, 16, 32, cols), A[:, cols], atol=1e-13)
+    np.testing.assert_allclose(oracle.adjoint_measurements_kron(s.mask, 6, 5, 16, 32, s.y), A.conj().T @ s.y,
+                               atol=1e-12)
