@@ -348,6 +348,117 @@ def run_gpu(args, rank, world, local_rank):
     return 0
 
 
+# ------------------------------------------------------------------------------------------
+# secondary workloads (one JSON line each; the default run is the batched 256x256 metric)
+# ------------------------------------------------------------------------------------------
+
+
+def _solve_timed(bccb, torch, insts, algo, iters, rho=1.0, prec="f32", reps=3, check=False):
+    stream = torch.cuda.Stream()
+    solver = bccb.BatchSolver(insts, algo, rho, stream=stream, prec=prec)
+    cdt = torch.complex128 if prec == "f64" else torch.complex64
+    y = torch.from_numpy(solver.y_host).cuda()
+    c = torch.zeros(solver.total_c, dtype=cdt, device="cuda")
+    aux = torch.zeros_like(c) if algo == "admm" else None
+    torch.cuda.synchronize()
+    if prec == "f32":
+        bccb.bccb_batch_tune(solver.handle, y, 10, None)
+    bccb.bccb_set_timing(solver.handle, True)
+    solver.solve(y, iters, c, aux_out=aux, check=check)  # warm-up
+    times = []
+    for _ in range(reps):
+        solver.solve(y, iters, c, aux_out=aux, check=check)
+        times.append(bccb.bccb_last_timing(solver.handle))
+    res = solver.results() if check else None
+    torch.cuda.synchronize()
+    out = (c.cpu().numpy(), None if aux is None else aux.cpu().numpy())
+    solver.close()
+    tot = [t["setup_ms"] + t["iterate_ms"] + t["check_ms"] for t in times]
+    return out, {"ms": statistics.median(tot), "iterate_ms": statistics.median(t["iterate_ms"] for t in times),
+                 "setup_ms": statistics.median(t["setup_ms"] for t in times)}, res
+
+
+def run_workload(args):
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2509_13592_gb300 as bccb
+    import synth
+
+    torch.cuda.set_device(0)
+    if args.workload == "ragged":
+        B, T = args.batch, args.iters
+        snaps = synth.config_batch(3, B)
+        insts = [dict(M1=s.M1, M2=s.M2, L1=s.L1, L2=s.L2, mask=s.mask, y=s.y, lam=0.1, lam_is_frac=True)
+                 for s in snaps]
+        _, t, _ = _solve_timed(bccb, torch, insts, "fista", T, check=True)
+        elems = sum(s.L1 * s.L2 for s in snaps)
+        line = {"workload": f"ragged FISTA batch: {B} snapshots, L1,L2 uniform on {{64,128,256}}, M_i = L_i/4, "
+                            f"25% occupancy, K in 1..10, SNR 0..30 dB, {T} iterations",
+                "value": B * T / (t["ms"] / 1e3), "unit": "instance-iterations/s", "phases_ms": t,
+                "grid_elements": elems, "flop_rate_tflops": sum(flops_per_inst_iter(s.L1, s.L2) for s in snaps)
+                * T / (t["iterate_ms"] / 1e3) / 1e12}
+    elif args.workload == "precision1024":
+        s = synth.config_snapshot(4, 0)
+        inst = [dict(M1=s.M1, M2=s.M2, L1=s.L1, L2=s.L2, mask=s.mask, y=s.y, lam=0.05, lam_is_frac=True)]
+        T = args.iters
+        (c32, a32), t32, r32 = _solve_timed(bccb, torch, inst, "admm", T, rho=0.5, prec="f32", reps=1, check=True)
+        (c64, a64), t64, r64 = _solve_timed(bccb, torch, inst, "admm", T, rho=0.5, prec="f64", reps=1, check=True)
+        n64 = np.linalg.norm(c64)
+        line = {"workload": f"1024x1024 grid, 64x64 array N=1024, 20 off-grid sources, 15 dB, ADMM rho=0.5, "
+                            f"lam=0.05||A^H y||_inf, {T} iterations, single snapshot",
+                "fp32_ms": t32, "fp64_ms": t64,
+                "rel_err_z_fp32_vs_fp64": float(np.linalg.norm(c32 - c64) / n64) if n64 > 0 else None,
+                "rel_err_c_fp32_vs_fp64": float(np.linalg.norm(a32 - a64) / np.linalg.norm(a64)),
+                "nnz_fp32": int(np.count_nonzero(c32)), "nnz_fp64": int(np.count_nonzero(c64)),
+                "kkt_fp32": float(r32["kkt"][0]), "kkt_fp64": float(r64["kkt"][0]),
+                "objective_fp32": float(r32["objective"][0]), "objective_fp64": float(r64["objective"][0])}
+    elif args.workload == "single64":
+        s = synth.config_snapshot(1, 0)
+        inst = [dict(M1=s.M1, M2=s.M2, L1=s.L1, L2=s.L2, mask=s.mask, y=s.y, lam=0.1, lam_is_frac=True)]
+        _, t, _ = _solve_timed(bccb, torch, inst, "fista", 500, reps=5, check=True)
+        line = {"workload": "single snapshot: 16x16 array, N=64, 64x64 grid, 3 on-grid sources, 20 dB, FISTA 500 "
+                            "iterations, lam=0.1||A^H y||_inf", "latency_ms": t,
+                "per_iteration_us": 1e3 * t["iterate_ms"] / 500}
+    elif args.workload == "table1":
+        rows = []
+        for algo in ("ista", "fista", "admm"):
+            for L1 in (64, 128, 256, 512):
+                for it in (50, 100, 200, 400):
+                    errs, errs32, t_reg, t_gpu = [], [], [], []
+                    for trial in range(args.trials):
+                        s = synth.paper_experiment_snapshot(trial, L1)
+                        A = oracle.dictionary(s.mask, s.M1, s.M2, s.L1, s.L2)
+                        lam = 0.1 * oracle.lambda_max(A, s.y)
+                        t0 = time.perf_counter()
+                        if algo == "ista":
+                            ref = oracle.ista(A, s.y, lam, it)
+                        elif algo == "fista":
+                            ref = oracle.fista(A, s.y, lam, it)
+                        else:
+                            ref = oracle.admm(A, s.y, lam, float(s.N), it)[0]
+                        t_reg.append(1e3 * (time.perf_counter() - t0))
+                        inst = [dict(M1=s.M1, M2=s.M2, L1=s.L1, L2=s.L2, mask=s.mask, y=s.y, lam=lam)]
+                        (c64, _), t64, _ = _solve_timed(bccb, torch, inst, algo, it, rho=float(s.N), prec="f64",
+                                                        reps=1)
+                        (c32, _), t32, _ = _solve_timed(bccb, torch, inst, algo, it, rho=float(s.N), reps=1)
+                        nr = np.linalg.norm(ref)
+                        errs.append(float(np.linalg.norm(c64 - ref) / nr) if nr else 0.0)
+                        errs32.append(float(np.linalg.norm(c32 - ref) / nr) if nr else 0.0)
+                        t_gpu.append(t32["ms"])
+                    rows.append({"algo": algo, "L1": L1, "n_iter": it, "eps_r_fp64_gpu": float(np.mean(errs)),
+                                 "eps_r_fp32_gpu": float(np.mean(errs32)), "t_reg_cpu_ms": float(np.mean(t_reg)),
+                                 "t_fast_gpu_ms": float(np.mean(t_gpu))})
+        line = {"workload": f"paper experiment shape: M1=51, M2=16, N=40, L2=32, 15 dB, K in 1..10, "
+                            f"{args.trials} trials; ADMM rho = N", "rows": rows, "cpu_cores": os.cpu_count()}
+    else:
+        raise SystemExit(f"unknown workload {args.workload}")
+    line["impl"] = "ours"
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -359,6 +470,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-1e-4 measurement")
     ap.add_argument("--tune-cache", default=None, help="autotuner cache file (default: measure every run)")
+    ap.add_argument("--workload", default="batched256",
+                    choices=["batched256", "ragged", "precision1024", "single64", "table1"],
+                    help="batched256 is the benchmark metric; the others print their own line")
+    ap.add_argument("--trials", type=int, default=3, help="trials per Table I cell (--workload table1)")
     ap.add_argument("--traffic-bytes", type=float, default=None,
                     help="DRAM bytes per launch of the fused kernel from an ncu capture")
     args = ap.parse_args()
@@ -367,6 +482,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload != "batched256":
+        return run_workload(args)
     return run_gpu(args, rank, world, local_rank)
 
 

@@ -38,6 +38,16 @@ int fail(bccb_solver* s, int code, const std::string& msg) {
     if (e_ != cudaSuccess) return fail((s), BCCB_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
+// A timing event: inside a stream capture it must become an external event-record node
+// to be readable after a graph launch; outside a capture a plain record.
+cudaError_t record_timing(bccb_solver* s, int i) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(s->stream, &cs);
+  if (e != cudaSuccess) return e;
+  if (cs == cudaStreamCaptureStatusActive) return cudaEventRecordWithFlags(s->ev[i], s->stream, cudaEventRecordExternal);
+  return cudaEventRecord(s->ev[i], s->stream);
+}
+
 template <typename T>
 cudaError_t dalloc(T** p, size_t count) {
   if (count == 0) count = 1;
@@ -259,11 +269,11 @@ int bccb_batch_solve(bccb_solver_t s, const void* y_dev, int iters, const void* 
   if (iters < 1) return fail(s, BCCB_ERR_INVALID_ARG, "iters must be >= 1");
   BCCB_CUDA(s, cudaSetDevice(s->device));
   s->launches = 0;
-  if (s->timing) BCCB_CUDA(s, cudaEventRecordWithFlags(s->ev[0], s->stream, cudaEventRecordExternal));
+  if (s->timing) BCCB_CUDA(s, record_timing(s, 0));
   if (s->algo == BCCB_FISTA) BCCB_CUDA(s, bccb::fista_schedule(s, iters));
   const void* y = y_dev;
   BCCB_CUDA(s, bccb::run_setup(s, y));
-  if (s->timing) BCCB_CUDA(s, cudaEventRecordWithFlags(s->ev[1], s->stream, cudaEventRecordExternal));
+  if (s->timing) BCCB_CUDA(s, record_timing(s, 1));
   FusedArgs a{};
   a.insts = s->d_fused;
   a.beta = (s->algo == BCCB_FISTA) ? s->d_beta : nullptr;
@@ -295,9 +305,9 @@ int bccb_batch_solve(bccb_solver_t s, const void* y_dev, int iters, const void* 
       BCCB_CUDA(s, cudaStreamWaitEvent(s->stream, s->class_done[k], 0));
     }
   }
-  if (s->timing) BCCB_CUDA(s, cudaEventRecordWithFlags(s->ev[2], s->stream, cudaEventRecordExternal));
+  if (s->timing) BCCB_CUDA(s, record_timing(s, 2));
   if (check) BCCB_CUDA(s, bccb::run_check(s, y, c_out_dev));
-  if (s->timing) BCCB_CUDA(s, cudaEventRecordWithFlags(s->ev[3], s->stream, cudaEventRecordExternal));
+  if (s->timing) BCCB_CUDA(s, record_timing(s, 3));
   s->last_checked = check != 0;
   return BCCB_OK;
 }
