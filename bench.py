@@ -199,8 +199,11 @@ def run_gpu(args, rank, world, local_rank):
         import torch.distributed as dist
 
         dist.init_process_group("nccl")
+    from paper_2509_13592_gb300 import shard
+
     B, T = args.batch, args.iters
-    snaps = make_batch(B, rank * B)
+    mine = shard.contiguous_range(B, rank)  # weak scaling: every rank solves its own B snapshots
+    snaps = make_batch(B, mine.start)
     insts = [dict(M1=s.M1, M2=s.M2, L1=s.L1, L2=s.L2, mask=s.mask, y=s.y, lam=WORKLOAD["lam_frac"],
                   lam_is_frac=True) for s in snaps]
     stream = torch.cuda.Stream()  # graph capture needs a non-default stream
@@ -241,11 +244,7 @@ def run_gpu(args, rank, world, local_rank):
             launches += t["launches"]
         end.record(stream)
         barrier()
-    elapsed = start.elapsed_time(end) / 1e3
-    if dist is not None:
-        t_all = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
-        elapsed = float(t_all.item())
+    elapsed = shard.max_over_ranks(start.elapsed_time(end) / 1e3, device="cuda")
     value = world * B * T * args.steps / elapsed
     clock = clocks.summary()
 
@@ -264,11 +263,7 @@ def run_gpu(args, rank, world, local_rank):
     for _ in range(args.steps):
         bccb.bccb_batch_solve_host_ptr(solver.handle, y_pin.data_ptr(), T, c_pin.data_ptr(), True)
     barrier()
-    e2e_elapsed = time.perf_counter() - t0
-    if dist is not None:
-        t_all = torch.tensor([e2e_elapsed], device="cuda")
-        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
-        e2e_elapsed = float(t_all.item())
+    e2e_elapsed = shard.max_over_ranks(time.perf_counter() - t0, device="cuda")
     e2e_value = world * B * T * args.steps / e2e_elapsed
 
     # ---- iterations (and time) until every sampled instance is within 1e-4 of its

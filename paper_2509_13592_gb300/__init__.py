@@ -6,7 +6,7 @@ the library exists.  Any use of the binding raises ImportError when
 """
 import importlib
 
-_SUBMODULES = {"binding", "build", "learned"}
+_SUBMODULES = {"binding", "build", "learned", "shard"}
 
 
 def __getattr__(name):
