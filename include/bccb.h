@@ -164,7 +164,8 @@ int bccb_batch_tile(bccb_solver_t s, int L1, int L2, int* tile);
  * bccb_unrolled_bwd takes grad_c_dev = dLoss/dc_{K-1} (complex64, packed like c, as
  * dLoss/dRe + j dLoss/dIm) and ADDS dLoss/da_k and dLoss/dt_k, summed over the batch,
  * to the device float64 arrays grad_scale_dev / grad_thresh_dev (length layers).  It
- * needs the same solver, layers, multipliers and saved buffer as the forward call. */
+ * needs the same solver, layers, multipliers and saved buffer as the forward call.
+ * Square grids (L1 = L2, up to 256) only; BCCB_ERR_UNSUPPORTED otherwise. */
 int bccb_unrolled_fwd(bccb_solver_t s, const void* y_dev, int layers, const float* scale_dev,
                       const float* thresh_dev, void* c_out_dev, void* saved_dev, int check);
 int bccb_unrolled_bwd(bccb_solver_t s, int layers, const float* scale_dev, const float* thresh_dev,

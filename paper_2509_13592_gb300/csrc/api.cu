@@ -270,13 +270,13 @@ int bccb_batch_solve(bccb_solver_t s, const void* y_dev, int iters, const void* 
   BCCB_CUDA(s, cudaSetDevice(s->device));
   s->launches = 0;
   if (s->timing) BCCB_CUDA(s, record_timing(s, 0));
-  if (s->algo == BCCB_FISTA) BCCB_CUDA(s, bccb::fista_schedule(s, iters));
+  if (s->algo != BCCB_ADMM) BCCB_CUDA(s, bccb::fista_schedule(s, iters));
   const void* y = y_dev;
   BCCB_CUDA(s, bccb::run_setup(s, y));
   if (s->timing) BCCB_CUDA(s, record_timing(s, 1));
   FusedArgs a{};
   a.insts = s->d_fused;
-  a.beta = (s->algo == BCCB_FISTA) ? s->d_beta : nullptr;
+  a.beta = (s->algo != BCCB_ADMM) ? s->d_beta : nullptr;
   a.twiddle = s->d_tw32;
   a.mult = s->d_mult;
   a.bt = s->d_cterm;
@@ -423,7 +423,7 @@ int bccb_batch_capture(bccb_solver_t s, const void* y_dev, int iters, const void
   if (s->stream == nullptr)
     return fail(s, BCCB_ERR_INVALID_ARG, "graph capture needs a non-default stream");
   // anything that may allocate happens before the capture
-  if (s->algo == BCCB_FISTA) BCCB_CUDA(s, bccb::fista_schedule(s, iters));
+  if (s->algo != BCCB_ADMM) BCCB_CUDA(s, bccb::fista_schedule(s, iters));
   BCCB_CUDA(s, cudaStreamSynchronize(s->stream));
   if (s->graph) {
     cudaGraphExecDestroy(s->graph);
@@ -478,7 +478,7 @@ int bccb_batch_tune(bccb_solver_t s, const void* y_dev, int probe_iters, const c
     if (!c.multipass && !cached.count(std::make_tuple(c.entry.L1, c.entry.L2, admm))) need_probe = true;
   FILE* out = nullptr;
   if (need_probe) {
-    if (s->algo == BCCB_FISTA) BCCB_CUDA(s, bccb::fista_schedule(s, probe_iters));
+    if (s->algo != BCCB_ADMM) BCCB_CUDA(s, bccb::fista_schedule(s, probe_iters));
     if (!s->d_probe) BCCB_CUDA(s, dalloc(&s->d_probe, s->total_c));
     BCCB_CUDA(s, bccb::run_setup(s, y_dev));
     if (cache_path) out = fopen(cache_path, "a");
@@ -503,7 +503,7 @@ int bccb_batch_tune(bccb_solver_t s, const void* y_dev, int probe_iters, const c
     FusedArgs a{};
     a.insts = s->d_fused;
     a.ids = s->d_ids + c.first;
-    a.beta = (s->algo == BCCB_FISTA) ? s->d_beta : nullptr;
+    a.beta = (s->algo != BCCB_ADMM) ? s->d_beta : nullptr;
     a.twiddle = s->d_tw32;
     a.mult = s->d_mult;
     a.bt = s->d_cterm;
@@ -571,8 +571,11 @@ int bccb_unrolled_fwd(bccb_solver_t s, const void* y_dev, int layers, const floa
   a.save_stride = s->total_c;
   a.iters = layers;
   for (const auto& c : s->classes) {
+    const bccb::FusedEntry* le = bccb::learned_lookup(c.L1, c.L2);
+    if (!le) return fail(s, BCCB_ERR_UNSUPPORTED, "the unrolled network needs square grids (L1 = L2)");
+    BCCB_CUDA(s, le->prepare());
     a.ids = s->d_ids + c.first;
-    BCCB_CUDA(s, c.entry.launch(a, c.count, s->stream));
+    BCCB_CUDA(s, le->launch(a, c.count, s->stream));
     s->launches += 1;
   }
   if (check) BCCB_CUDA(s, bccb::run_check(s, y, c_out_dev));

@@ -40,6 +40,12 @@ const FusedEntry* BCCB_CAT(fused_lookup_L2_, BCCB_L2)(int L1, bool admm, int til
   return nullptr;
 }
 
+// forward pass of the unrolled network (per-layer multipliers, saved layer inputs): square grids
+const FusedEntry* BCCB_CAT(learned_lookup_L2_, BCCB_L2)(int L1) {
+  static const FusedEntry e = fused_entry<BCCB_L2, BCCB_L2, false, kFusedTileElems, true>();
+  return L1 == BCCB_L2 ? &e : nullptr;
+}
+
 const AdjointEntry* BCCB_CAT(adjoint_lookup_L2_, BCCB_L2)(int L1) {
   static const AdjointEntry table[] = {adjoint_entry<16, BCCB_L2>(), adjoint_entry<32, BCCB_L2>(),
                                        adjoint_entry<64, BCCB_L2>(), adjoint_entry<128, BCCB_L2>(),

@@ -53,7 +53,7 @@ struct FusedInst {
 struct FusedArgs {
   const FusedInst* insts;  // device array of instances
   const int* ids;          // instance index for cluster k = blockIdx.x / C
-  const float* beta;       // FISTA momentum beta_t (length iters); nullptr for ISTA
+  const float* beta;       // momentum beta_t (length iters); zeros or nullptr for ISTA
   const float2* twiddle;   // W_1024^e, e = 0..1023 (float2)
   const float* mult;       // Fourier multiplier q (includes 1/(L1 L2)), natural order [p2][p1]
   const float2* bt;        // Fourier-domain constant term Bt, natural order [p2][p1]
@@ -494,7 +494,9 @@ __device__ __forceinline__ void cluster_barrier() {
   }
 }
 
-template <int L1, int L2, bool ADMM, int TILE>
+// LEARN: honour FusedArgs::scale / ::thresh / ::save (the unrolled network's forward pass);
+// plain solves are compiled without them.
+template <int L1, int L2, bool ADMM, int TILE, bool LEARN = false>
 __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<L1, L2, ADMM, TILE>::MIN_BLOCKS)
     fused_solve_kernel(const FusedArgs a) {
   using S = FusedShape<L1, L2, ADMM, TILE>;
@@ -549,7 +551,8 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
   }
   __syncthreads();
 
-  const bool fista = (a.beta != nullptr) && !ADMM;
+  // ISTA runs as FISTA with every momentum weight 0 (a zero table, or no table):
+  // c + 0 (c - c_prev) = c exactly, so the iterates are ISTA's.
 
   // The pointwise update of one element after the inverse transform: returns the
   // next iteration's FFT input (z for ISTA/FISTA, z - v for ADMM).
@@ -557,21 +560,23 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
     const int sidx = row * L1 + e;
     if constexpr (!ADMM) {
       const float2 c_old = cta.s0[sidx];
-      const float2 x = fista ? cta.s1[sidx] : c_old;  // z^(t)
-      if (save_t) {
-        const int gidx = (crank + C * row) * L1 + e;
-        save_t[gidx] = x;
-        save_t[a.save_stride + gidx] = g;
+      const float2 x = cta.s1[sidx];  // z^(t)
+      float2 un;
+      if constexpr (LEARN) {
+        if (save_t) {
+          const int gidx = (crank + C * row) * L1 + e;
+          save_t[gidx] = x;
+          save_t[a.save_stride + gidx] = g;
+        }
+        un = make_float2(x.x - sc * g.x, x.y - sc * g.y);
+      } else {
+        un = make_float2(x.x - g.x, x.y - g.y);
       }
-      const float2 un = make_float2(x.x - sc * g.x, x.y - sc * g.y);
       const float2 cn = soft_threshold(un, kap);
       cta.s0[sidx] = cn;
-      if (fista) {
-        const float2 zn = make_float2(cn.x + beta * (cn.x - c_old.x), cn.y + beta * (cn.y - c_old.y));
-        cta.s1[sidx] = zn;
-        return zn;
-      }
-      return cn;
+      const float2 zn = make_float2(cn.x + beta * (cn.x - c_old.x), cn.y + beta * (cn.y - c_old.y));
+      cta.s1[sidx] = zn;
+      return zn;
     } else {
       const float2 zo = cta.s0[sidx];
       const float2 vo = cta.s1[sidx];
@@ -588,16 +593,22 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
   };
   // per-iteration multipliers of the unrolled network (1 and kappa otherwise)
   auto layer = [&](int it, float& sc, float& kap, float2*& save_t) {
-    sc = a.scale ? __ldg(&a.scale[it]) : 1.0f;
-    kap = a.thresh ? __ldg(&a.thresh[it]) * kappa : kappa;
-    save_t = a.save ? a.save + (int64_t)(2 * it) * a.save_stride + in.c_off : nullptr;
+    if constexpr (LEARN) {
+      sc = a.scale ? __ldg(&a.scale[it]) : 1.0f;
+      kap = a.thresh ? __ldg(&a.thresh[it]) * kappa : kappa;
+      save_t = a.save ? a.save + (int64_t)(2 * it) * a.save_stride + in.c_off : nullptr;
+    } else {
+      sc = 1.0f;
+      kap = kappa;
+      save_t = nullptr;
+    }
   };
 
   if constexpr (S::SQ16) {
     const int nz = kc / 16;
     cta.sq_fwd1_from_work();
     for (int it = 0; it < a.iters; ++it) {
-      const float beta = fista ? __ldg(&a.beta[it]) : 0.0f;
+      const float beta = a.beta ? __ldg(&a.beta[it]) : 0.0f;
       const bool last = (it == a.iters - 1);
       cta.sq_fwd2(nz);
       __syncthreads();
@@ -616,7 +627,7 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
     }
   } else {
     for (int it = 0; it < a.iters; ++it) {
-      const float beta = fista ? __ldg(&a.beta[it]) : 0.0f;
+      const float beta = a.beta ? __ldg(&a.beta[it]) : 0.0f;
       const bool last = (it == a.iters - 1);
       cta.template row_fft_from<0, false>(
           [&](int row, int e, float2 x) {
@@ -661,18 +672,18 @@ struct FusedEntry {
   cudaError_t (*prepare)();
 };
 
-template <int L1, int L2, bool ADMM, int TILE>
+template <int L1, int L2, bool ADMM, int TILE, bool LEARN = false>
 cudaError_t fused_prepare() {
   using S = FusedShape<L1, L2, ADMM, TILE>;
-  cudaError_t e = cudaFuncSetAttribute(fused_solve_kernel<L1, L2, ADMM, TILE>,
+  cudaError_t e = cudaFuncSetAttribute(fused_solve_kernel<L1, L2, ADMM, TILE, LEARN>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
   if (e == cudaSuccess && S::C > 8)
-    e = cudaFuncSetAttribute(fused_solve_kernel<L1, L2, ADMM, TILE>, cudaFuncAttributeNonPortableClusterSizeAllowed,
-                             1);
+    e = cudaFuncSetAttribute(fused_solve_kernel<L1, L2, ADMM, TILE, LEARN>,
+                             cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   return e;
 }
 
-template <int L1, int L2, bool ADMM, int TILE>
+template <int L1, int L2, bool ADMM, int TILE, bool LEARN = false>
 cudaError_t fused_launch(const FusedArgs& a, int n_inst, cudaStream_t st) {
   using S = FusedShape<L1, L2, ADMM, TILE>;
   if (n_inst <= 0) return cudaSuccess;
@@ -688,14 +699,14 @@ cudaError_t fused_launch(const FusedArgs& a, int n_inst, cudaStream_t st) {
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, fused_solve_kernel<L1, L2, ADMM, TILE>, a);
+  return cudaLaunchKernelEx(&cfg, fused_solve_kernel<L1, L2, ADMM, TILE, LEARN>, a);
 }
 
-template <int L1, int L2, bool ADMM, int TILE = kFusedTileElems>
+template <int L1, int L2, bool ADMM, int TILE = kFusedTileElems, bool LEARN = false>
 FusedEntry fused_entry() {
   using S = FusedShape<L1, L2, ADMM, TILE>;
-  return FusedEntry{L1, L2, ADMM ? 1 : 0, TILE, S::C, S::T, S::SMEM, &fused_launch<L1, L2, ADMM, TILE>,
-                    &fused_prepare<L1, L2, ADMM, TILE>};
+  return FusedEntry{L1, L2, ADMM ? 1 : 0, TILE, S::C, S::T, S::SMEM, &fused_launch<L1, L2, ADMM, TILE, LEARN>,
+                    &fused_prepare<L1, L2, ADMM, TILE, LEARN>};
 }
 
 }  // namespace bccb

@@ -10,6 +10,7 @@
 //                update of the state, and the next iteration's forward row DFTs.
 // V = float2 (complex64) or double2 (complex128); transforms are radix-4 Stockham
 // stages (one radix-2 stage for odd log2 n) staged in shared memory.
+#include "fft_smem.cuh"
 #include "solver.h"
 
 namespace bccb {
@@ -36,55 +37,6 @@ struct MpArgs {
   int last;
   double rho;
 };
-
-// Stockham FFT of `cnt` interleaved sequences of length n (element e of sequence q at
-// x[e * cnt + q]), ping-pong between x and y; returns the buffer that holds the result.
-template <typename V, bool INV>
-__device__ V* fft_smem(V* x, V* y, int n, int cnt, const V* __restrict__ tw) {
-  int Ns = 1;
-  while (Ns * 4 <= n) {
-    const int q4 = n >> 2;
-    const int step = kTwiddleLen / (4 * Ns);
-    for (int idx = threadIdx.x; idx < q4 * cnt; idx += blockDim.x) {
-      const int q = idx % cnt, j = idx / cnt;
-      const int kk = j % Ns;
-      V v0 = x[j * cnt + q], v1 = x[(j + q4) * cnt + q], v2 = x[(j + 2 * q4) * cnt + q],
-        v3 = x[(j + 3 * q4) * cnt + q];
-      if (Ns > 1) {
-        v1 = twmul<INV>(v1, tw[kk * step]);
-        v2 = twmul<INV>(v2, tw[2 * kk * step]);
-        v3 = twmul<INV>(v3, tw[3 * kk * step]);
-      }
-      dft4<INV>(v0, v1, v2, v3);
-      const int o = (j / Ns) * 4 * Ns + kk;
-      y[o * cnt + q] = v0;
-      y[(o + Ns) * cnt + q] = v1;
-      y[(o + 2 * Ns) * cnt + q] = v2;
-      y[(o + 3 * Ns) * cnt + q] = v3;
-    }
-    __syncthreads();
-    V* t = x;
-    x = y;
-    y = t;
-    Ns *= 4;
-  }
-  if (Ns < n) {
-    const int h = n >> 1;
-    const int step = kTwiddleLen / (2 * Ns);
-    for (int idx = threadIdx.x; idx < h * cnt; idx += blockDim.x) {
-      const int q = idx % cnt, j = idx / cnt;
-      const int kk = j % Ns;
-      const V a = x[j * cnt + q];
-      const V b = twmul<INV>(x[(j + h) * cnt + q], tw[kk * step]);
-      const int o = (j / Ns) * 2 * Ns + kk;
-      y[o * cnt + q] = cadd(a, b);
-      y[(o + Ns) * cnt + q] = csub(a, b);
-    }
-    __syncthreads();
-    x = y;
-  }
-  return x;
-}
 
 template <typename V>
 __device__ __forceinline__ V shrink(V u, typename ScalarOf<V>::T kappa) {
@@ -263,7 +215,8 @@ cudaError_t run_t(bccb_solver* s, const int* ids, int count, int iters, const vo
   const int cells = s->max_L1 * s->max_L2;
   const dim3 gcell((unsigned)count, (unsigned)min(64, (cells + kMpThreads - 1) / kMpThreads));
   const dim3 grow((unsigned)count, (unsigned)s->max_L2);
-  const int cpb = mp_cols_per_block(s->max_L2, (int)sizeof(V));
+  // a handful of instances: one column per block, so the few active columns still spread over many SMs
+  const int cpb = count <= 8 ? 1 : mp_cols_per_block(s->max_L2, (int)sizeof(V));
   const dim3 gcol((unsigned)count, (unsigned)((s->max_L1 + cpb - 1) / cpb));
   const size_t sm_row = 2 * (size_t)s->max_L1 * sizeof(V);
   const size_t sm_col = 2 * (size_t)s->max_L2 * cpb * sizeof(V);

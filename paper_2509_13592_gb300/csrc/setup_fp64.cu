@@ -13,12 +13,13 @@
 //     eq:admm as FFT2(b)/(Lambda + rho).
 //   * the final check: r = A^H (y - A c) = b - G c, the relative KKT residual of the
 //     1/2-scaled LASSO, and the objective 1/2 ||y - A c||^2 + lam ||c||_1.
-// The FP64 2D DFTs are plain radix-2 Stockham passes (rows, then columns) over
-// global memory with each row / column tile staged in shared memory.
+// The FP64 2D DFTs are radix-4 Stockham passes (rows, then columns) over global
+// memory with each row / column tile staged in shared memory.
 #include <math.h>
 
 #include <vector>
 
+#include "fft_smem.cuh"
 #include "solver.h"
 
 namespace bccb {
@@ -26,27 +27,6 @@ namespace bccb {
 namespace {
 
 constexpr int kThreads = 256;
-
-__device__ double2* stockham64(double2* x, double2* y, int n, int cnt, int inv, const double2* tw) {
-  const int half = n >> 1;
-  for (int Ns = 1; Ns < n; Ns <<= 1) {
-    for (int idx = threadIdx.x; idx < half * cnt; idx += blockDim.x) {
-      const int q = idx % cnt, j = idx / cnt;
-      double2 a = x[j * cnt + q], b = x[(j + half) * cnt + q];
-      const int kk = j & (Ns - 1);
-      const double2 w = tw[kk * (kTwiddleLen / (2 * Ns))];
-      b = inv ? cmulc(b, w) : cmul(b, w);
-      const int o = ((j - kk) << 1) + kk;
-      y[o * cnt + q] = cadd(a, b);
-      y[(o + Ns) * cnt + q] = csub(a, b);
-    }
-    __syncthreads();
-    double2* t = x;
-    x = y;
-    y = t;
-  }
-  return x;
-}
 
 // In-place DFT of every row (length L1) of every instance's grid.
 __global__ void fft64_rows_kernel(const InstDesc* __restrict__ desc, double2* base, int inv,
@@ -59,7 +39,7 @@ __global__ void fft64_rows_kernel(const InstDesc* __restrict__ desc, double2* ba
   double2* g = base + d.g_off + (int64_t)blockIdx.y * d.L1;
   for (int e = threadIdx.x; e < d.L1; e += blockDim.x) x[e] = g[e];
   __syncthreads();
-  const double2* out = stockham64(x, y, d.L1, 1, inv, tw);
+  const double2* out = inv ? fft_smem<double2, true>(x, y, d.L1, 1, tw) : fft_smem<double2, false>(x, y, d.L1, 1, tw);
   for (int e = threadIdx.x; e < d.L1; e += blockDim.x) g[e] = out[e];
 }
 
@@ -82,7 +62,8 @@ __global__ void fft64_cols_kernel(const InstDesc* __restrict__ desc, double2* ba
     x[idx] = g[(int64_t)e * d.L1 + c0 + q];
   }
   __syncthreads();
-  const double2* out = stockham64(x, y, d.L2, cnt, inv, tw);
+  const double2* out =
+      inv ? fft_smem<double2, true>(x, y, d.L2, cnt, tw) : fft_smem<double2, false>(x, y, d.L2, cnt, tw);
   for (int idx = threadIdx.x; idx < d.L2 * cnt; idx += blockDim.x) {
     const int e = idx / cnt, q = idx % cnt;
     g[(int64_t)e * d.L1 + c0 + q] = out[idx];
@@ -357,8 +338,15 @@ cudaError_t fista_schedule(bccb_solver* s, int iters) {
     if (err != cudaSuccess) return err;
     s->beta_cap = iters;
   }
-  fista_beta_kernel<<<1, 32, 0, s->stream>>>(s->d_beta, s->d_beta64, iters);
-  s->launches += 1;
+  if (s->algo == 0) {  // ISTA: FISTA with zero momentum
+    cudaError_t err = cudaMemsetAsync(s->d_beta, 0, (size_t)iters * sizeof(float), s->stream);
+    if (err == cudaSuccess && s->d_beta64)
+      err = cudaMemsetAsync(s->d_beta64, 0, (size_t)iters * sizeof(double), s->stream);
+    if (err != cudaSuccess) return err;
+  } else {
+    fista_beta_kernel<<<1, 32, 0, s->stream>>>(s->d_beta, s->d_beta64, iters);
+    s->launches += 1;
+  }
   s->beta_len = iters;
   return cudaGetLastError();
 }

@@ -115,4 +115,6 @@ cudaError_t run_multipass(bccb_solver* s, const int* ids, int count, int iters, 
 // fused_inst.cu / fused_dispatch.cu: tile 0 = the default 8192-element tile
 const FusedEntry* fused_lookup(int L1, int L2, bool admm, int tile = 0);
 const AdjointEntry* adjoint_lookup(int L1, int L2);
+// the unrolled network's forward kernel (square grids L1 = L2, FISTA, default tile)
+const FusedEntry* learned_lookup(int L1, int L2);
 }  // namespace bccb
