@@ -58,6 +58,10 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, false, TILE>::T, FusedShape
   cta.tw = reinterpret_cast<float2*>(sp);
   sp += NMAX * 8;
   cta.pmask = reinterpret_cast<uint16_t*>(sp);
+  sp += ((S::SH * 2 + 15) / 16) * 16;
+  cta.tw256 = reinterpret_cast<float2*>(sp);
+  sp += 256 * 8;
+  cta.tw16 = reinterpret_cast<float2*>(sp);
   cta.tid = threadIdx.x;
   int crank = 0;
   if constexpr (C > 1) crank = (int)cg::this_cluster().block_rank();

@@ -98,8 +98,11 @@ struct FusedShape {
   // rows of 256 = 16 x 16: a thread reads and writes the same 16 positions in the
   // last inverse and the first forward row stage (see FusedCta::sq_*)
   static constexpr bool SQ16 = ROW_WARP && (L1 == 256);
+  // middle stage with each 16-point butterfly split over 4 lanes (cluster path)
+  static constexpr bool SPLIT_MID = (C > 1) && (Q == 16) && (SH % L1 == 0);
   // work (padded) + two state grids + twiddles + a frequency bit mask per middle-stage pair
-  static constexpr int SMEM = (R * P + 2 * E) * 8 + NMAX * 8 + SH * 2;
+  // + W_256^{i j} (16 x 16, rows of 256) + W_16^m
+  static constexpr int SMEM = (R * P + 2 * E) * 8 + NMAX * 8 + ((SH * 2 + 15) / 16) * 16 + 256 * 8 + 16 * 8;
   // two CTAs per SM when their shared memory fits (227 KB per CTA, 228 KB per SM)
   static constexpr int MIN_BLOCKS = (2 * (SMEM + 1024) <= 228 * 1024) ? 2 : 1;
   static_assert(L1 >= 16 && L2 >= 16, "fused path needs L1, L2 >= 16");
@@ -162,6 +165,8 @@ struct FusedCta {
   float2* s1;       // E: z (FISTA) or v (ADMM)
   float2* tw;       // NMAX twiddles W_NMAX^e
   uint16_t* pmask;  // SH: bit q set when frequency (k1 + RP q, col) of pair pl has q != 0
+  float2* tw256;    // 16 x 16: tw256[i * 16 + j] = W_256^{i j} (conflict-free per-lane twiddles)
+  float2* tw16;     // W_16^m, m < 16
   int crank;
   int tid;
 
@@ -314,7 +319,7 @@ struct FusedCta {
     for (int i = 0; i < 16; ++i) v[i] = work[row * P + pad16(j + 16 * i)];
     __syncwarp();
 #pragma unroll
-    for (int i = 1; i < 16; ++i) v[i] = twmul<false>(v[i], tw[i * j * (NMAX / 256)]);
+    for (int i = 1; i < 16; ++i) v[i] = twmul<false>(v[i], tw256[i * 16 + j]);
     if (nz == 1) {
       float2 s0 = v[0];
 #pragma unroll
@@ -326,7 +331,7 @@ struct FusedCta {
 #pragma unroll
       for (int i = 1; i < 16; ++i) {
         s0 = cadd(s0, v[i]);
-        s1 = cadd(s1, twmul<false>(v[i], tw[i * (NMAX / 16)]));
+        s1 = cadd(s1, twmul<false>(v[i], tw16[i]));
       }
       work[row * P + pad16(j)] = s0;
       work[row * P + pad16(j + 16)] = s1;
@@ -349,7 +354,7 @@ struct FusedCta {
       const float2 b = (nz == 2) ? work[row * P + pad16(j + 16)] : make_float2(0.f, 0.f);
       __syncwarp();
 #pragma unroll
-      for (int k = 0; k < 16; ++k) v[k] = cadd(a, twmul<true>(b, tw[k * (NMAX / 16)]));
+      for (int k = 0; k < 16; ++k) v[k] = cadd(a, twmul<true>(b, tw16[k]));
     } else {
 #pragma unroll
       for (int i = 0; i < 16; ++i) v[i] = (i < nz) ? work[row * P + pad16(j + 16 * i)] : make_float2(0.f, 0.f);
@@ -372,7 +377,7 @@ struct FusedCta {
     for (int i = 0; i < 16; ++i) v[i] = work[row * P + pad16(j + 16 * i)];
     __syncwarp();
 #pragma unroll
-    for (int i = 1; i < 16; ++i) v[i] = twmul<true>(v[i], tw[i * j * (NMAX / 256)]);
+    for (int i = 1; i < 16; ++i) v[i] = twmul<true>(v[i], tw256[i * 16 + j]);
     Dft<16, true, float2>::run(v);
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = epi(row, j + 16 * i, v[i]);
@@ -387,6 +392,8 @@ struct FusedCta {
   // twiddles and the per-pair frequency masks (bt may be null: a Gram product alone)
   __device__ __forceinline__ void load_tables(const float2* twiddle, const float* mult, const float2* bt) {
     for (int e = tid; e < NMAX; e += T) tw[e] = twiddle[e * (kTwiddleLen / NMAX)];
+    for (int e = tid; e < 256; e += T) tw256[e] = twiddle[((e >> 4) * (e & 15)) * (kTwiddleLen / 256)];
+    for (int e = tid; e < 16; e += T) tw16[e] = twiddle[e * (kTwiddleLen / 16)];
     for (int pl = tid; pl < SH; pl += T) {
       const int p = crank * SH + pl;
       const int k1 = p / L1, col = p % L1;
@@ -399,10 +406,106 @@ struct FusedCta {
     }
   }
 
+
+  // ---------------------------------------------------------------------------------------
+  // The middle stage with each pair's 16-point butterflies split over 4 lanes (4 x 4):
+  // lane e of a pair holds groups g = e + 4 i (i < 4); inner 4-point DFT over i, twiddle
+  // W_16^{e k'}, a 4 x 4 transpose across the lanes (four shuffle rounds), outer 4-point DFT
+  // over e, giving frequencies k' + 4 k'' on lane k'; then q . X - Bt and the mirror image
+  // back to groups.  The active pairs (columns < kc) are spread over all of the CTA's warps.
+  // ---------------------------------------------------------------------------------------
+  // 4 x 4 transpose across the 4 lanes of a pair: lane e's a[k] goes to lane k's a[e].
+  // Round r moves the entries with k - e = -r (mod 4); lane-dependent indices are resolved
+  // with selects over constant indices so that the values stay in registers.
+  static __device__ __forceinline__ void transpose4(float2 (&a)[4], int e, int lane) {
+    float2 out[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int si = (e - r) & 3, di = (e + r) & 3;
+      float2 send = a[0];
+#pragma unroll
+      for (int j = 1; j < 4; ++j) send = (si == j) ? a[j] : send;
+      const int src = (lane & ~3) | di;
+      float2 got;
+      got.x = __shfl_sync(0xffffffffu, send.x, src);
+      got.y = __shfl_sync(0xffffffffu, send.y, src);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) out[j] = (di == j) ? got : out[j];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = out[i];
+  }
+
+  __device__ __forceinline__ void middle_split(const uint32_t* peer, const float* mult_g, const float2* bt_g,
+                                               int kc) {
+    constexpr int KPO = SH / L1;  // frequencies k1 owned by this CTA, all columns each
+    const int np = KPO * kc;     // active pairs
+    const int lane = tid & 31, e = tid & 3;
+    const int rounds = (4 * np + T - 1) / T;
+    // shared::cluster base of the CTA holding each of this lane's groups e + 4 i
+    uint32_t base[4];
+    const uint32_t w = smem_addr(work);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) base[i] = cluster_map(w, (e + 4 * i) % C);
+    (void)peer;
+    for (int rd = 0; rd < rounds; ++rd) {
+      const int t = rd * T + tid;
+      const bool on = t < 4 * np;
+      const int a = on ? (t >> 2) : 0;
+      const int k1 = crank * KPO + a / kc, col = a % kc;
+      const int pl = (k1 - crank * KPO) * L1 + col;
+      const uint32_t pm = on ? pmask[pl] : 0u;
+      float2 v[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int g = e + 4 * i;
+        const int off = ((g / C) + QV * k1) * P + pad16(col);
+        v[i] = pm ? ld_cluster(base[i] + off * 8) : make_float2(0.f, 0.f);
+        if (g) v[i] = twmul<false>(v[i], tw[g * k1 * (NMAX / L2)]);
+      }
+      dft4<false>(v[0], v[1], v[2], v[3]);
+#pragma unroll
+      for (int i = 1; i < 4; ++i) v[i] = twmul<false>(v[i], tw16[e * i]);
+      transpose4(v, e, lane);
+      dft4<false>(v[0], v[1], v[2], v[3]);  // v[k''] = X[e + 4 k'']
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const int q = e + 4 * kk;
+        if (pm & (1u << q)) {
+          const int f = (k1 + RP * q) * L1 + col;
+          const float m = ld_ro_f32(&mult_g[f]);
+          const float2 b = bt_g ? ld_ro_f32x2(&bt_g[f]) : make_float2(0.f, 0.f);
+          v[kk] = make_float2(v[kk].x * m - b.x, v[kk].y * m - b.y);
+        } else {
+          v[kk] = make_float2(0.f, 0.f);
+        }
+      }
+      dft4<true>(v[0], v[1], v[2], v[3]);  // index e' of the inverse outer DFT
+      transpose4(v, e, lane);
+#pragma unroll
+      for (int i = 1; i < 4; ++i) v[i] = twmul<true>(v[i], tw16[e * i]);
+      dft4<true>(v[0], v[1], v[2], v[3]);  // v[i] -> group e + 4 i
+      if (on) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int g = e + 4 * i;
+          float2 o = v[i];
+          if (g) o = twmul<true>(o, tw[g * k1 * (NMAX / L2)]);
+          const int off = ((g / C) + QV * k1) * P + pad16(col);
+          st_cluster(base[i] + off * 8, o);
+        }
+      }
+    }
+  }
+
   // ---------------------------------------------------------------------------------------
   // cross-group radix-Q stage, Fourier-domain update, inverse radix-Q stage (in place)
   // ---------------------------------------------------------------------------------------
   __device__ __forceinline__ void middle(const uint32_t* peer, const float* mult_g, const float2* bt_g, int kc) {
+    if constexpr (S::SPLIT_MID) {
+      middle_split(peer, mult_g, bt_g, kc);
+      return;
+    }
     constexpr int PT = (SH + T - 1) / T;
 #pragma unroll
     for (int k = 0; k < PT; ++k) {
@@ -515,6 +618,10 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
   cta.tw = reinterpret_cast<float2*>(sp);
   sp += NMAX * 8;
   cta.pmask = reinterpret_cast<uint16_t*>(sp);
+  sp += ((S::SH * 2 + 15) / 16) * 16;
+  cta.tw256 = reinterpret_cast<float2*>(sp);
+  sp += 256 * 8;
+  cta.tw16 = reinterpret_cast<float2*>(sp);
   cta.tid = threadIdx.x;
   int crank = 0;
   if constexpr (C > 1) crank = (int)cg::this_cluster().block_rank();
