@@ -62,6 +62,10 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, false, TILE>::T, FusedShape
   cta.tw256 = reinterpret_cast<float2*>(sp);
   sp += 256 * 8;
   cta.tw16 = reinterpret_cast<float2*>(sp);
+  sp += 16 * 8;
+  cta.mtab = reinterpret_cast<float4*>(sp);
+  sp += S::MCAP * 16;
+  cta.poff = reinterpret_cast<uint16_t*>(sp);
   cta.tid = threadIdx.x;
   int crank = 0;
   if constexpr (C > 1) crank = (int)cg::this_cluster().block_rank();
@@ -77,7 +81,7 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, false, TILE>::T, FusedShape
 #pragma unroll
     for (int c = 0; c < C; ++c) peer[c] = (C > 1) ? cluster_map(w, c) : w;
   }
-  cta.load_tables(a.twiddle, mult, nullptr);
+  cta.load_tables(a.twiddle, mult, nullptr, kc);
   for (int idx = threadIdx.x; idx < E; idx += T) {
     const int s = idx / L1, e = idx % L1;
     cta.s0[idx] = a.grad_c[in.c_off + (crank + C * s) * L1 + e];

@@ -90,7 +90,6 @@ struct FusedShape {
   static constexpr int Q = cmin(16, L2);                          // cross-group radix
   static constexpr int QV = Q / C;                                // groups per CTA
   static constexpr int RP = L2 / Q;                               // local column DFT length
-  static constexpr int P = L1 + L1 / 16;                          // padded row pitch
   static constexpr int NMAX = cmax(L1, L2);
   static constexpr int SH = RP * L1 / C;                          // middle-stage pairs per CTA
   // each warp owns 512/L1 whole rows through every row stage
@@ -98,11 +97,21 @@ struct FusedShape {
   // rows of 256 = 16 x 16: a thread reads and writes the same 16 positions in the
   // last inverse and the first forward row stage (see FusedCta::sq_*)
   static constexpr bool SQ16 = ROW_WARP && (L1 == 256);
+  // padded row pitch; for rows of 256 one more element puts the two rows of a warp in
+  // different banks, so that their broadcast reads of the spectrum do not conflict
+  static constexpr int P = L1 + L1 / 16 + (SQ16 ? 1 : 0);
   // middle stage with each 16-point butterfly split over 4 lanes (cluster path)
   static constexpr bool SPLIT_MID = (C > 1) && (Q == 16) && (SH % L1 == 0);
+  // the split middle stage keeps up to MCAP of its nonzero (q, Bt) entries in shared
+  // memory (indexed through a per-pair offset); any beyond are read from global memory
+  static constexpr int MCAP = SPLIT_MID ? E / 16 : 0;
+  static constexpr int POFF = SPLIT_MID ? ((SH * 2 + 15) / 16) * 16 : 0;
   // work (padded) + two state grids + twiddles + a frequency bit mask per middle-stage pair
-  // + W_256^{i j} (16 x 16, rows of 256) + W_16^m
-  static constexpr int SMEM = (R * P + 2 * E) * 8 + NMAX * 8 + ((SH * 2 + 15) / 16) * 16 + 256 * 8 + 16 * 8;
+  // + W_256^{i j} (16 x 16, rows of 256) + W_16^m + the cached multipliers and offsets
+  static constexpr int SMEM = (R * P + 2 * E) * 8 + NMAX * 8 + ((SH * 2 + 15) / 16) * 16 + 256 * 8 + 16 * 8 +
+                              MCAP * 16 + POFF;
+  static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
+  static_assert((R * P * 8) % 16 == 0, "16-byte aligned layout after the work rows");
   // two CTAs per SM when their shared memory fits (227 KB per CTA, 228 KB per SM)
   static constexpr int MIN_BLOCKS = (2 * (SMEM + 1024) <= 228 * 1024) ? 2 : 1;
   static_assert(L1 >= 16 && L2 >= 16, "fused path needs L1, L2 >= 16");
@@ -167,6 +176,8 @@ struct FusedCta {
   uint16_t* pmask;  // SH: bit q set when frequency (k1 + RP q, col) of pair pl has q != 0
   float2* tw256;    // 16 x 16: tw256[i * 16 + j] = W_256^{i j} (conflict-free per-lane twiddles)
   float2* tw16;     // W_16^m, m < 16
+  float4* mtab;     // MCAP: {q, Bt.x, Bt.y, 0} of the active pairs' nonzero frequencies, in pair order
+  uint16_t* poff;   // per active pair: index of its first entry in mtab
   int crank;
   int tid;
 
@@ -368,13 +379,30 @@ struct FusedCta {
 
   // inverse second stage, the epilogue on its 16 outputs, and (unless last) the next
   // iteration's forward first stage on the 16 new inputs, all in registers
+  //
+  // With nz <= 2 the first inverse stage is folded in as well: its output at position
+  // j + 16 i is X[i] + W_16^{-j} X[i + 16], formed from the row's 2 x 16 nonzero inputs
+  // (read by all 16 threads of the row: broadcasts); otherwise sq_inv1 has run before.
   template <typename Epi>
-  __device__ __forceinline__ void sq_inv2_epi_fwd1(Epi&& epi, bool next) {
+  __device__ __forceinline__ void sq_inv2_epi_fwd1(Epi&& epi, bool next, int nz) {
     int row, j;
     sq_rowj(row, j);
     float2 v[16];
+    const float2* xr = work + row * P;
+    if (nz == 2) {
+      const float2 w = tw16[j];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = work[row * P + pad16(j + 16 * i)];
+      for (int i = 0; i < 16; ++i) v[i] = cadd(xr[pad16(i)], twmul<true>(xr[pad16(i + 16)], w));
+    } else if (nz == 1) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = xr[pad16(i)];
+    } else if (nz == 0) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = make_float2(0.f, 0.f);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = xr[pad16(j + 16 * i)];
+    }
     __syncwarp();
 #pragma unroll
     for (int i = 1; i < 16; ++i) v[i] = twmul<true>(v[i], tw256[i * 16 + j]);
@@ -390,7 +418,7 @@ struct FusedCta {
   }
 
   // twiddles and the per-pair frequency masks (bt may be null: a Gram product alone)
-  __device__ __forceinline__ void load_tables(const float2* twiddle, const float* mult, const float2* bt) {
+  __device__ __forceinline__ void load_tables(const float2* twiddle, const float* mult, const float2* bt, int kc) {
     for (int e = tid; e < NMAX; e += T) tw[e] = twiddle[e * (kTwiddleLen / NMAX)];
     for (int e = tid; e < 256; e += T) tw256[e] = twiddle[((e >> 4) * (e & 15)) * (kTwiddleLen / 256)];
     for (int e = tid; e < 16; e += T) tw16[e] = twiddle[e * (kTwiddleLen / 16)];
@@ -403,6 +431,43 @@ struct FusedCta {
         if (mult[f] != 0.f || (bt && (bt[f].x != 0.f || bt[f].y != 0.f))) pm |= 1u << q;
       }
       pmask[pl] = (uint16_t)pm;
+    }
+    if constexpr (S::SPLIT_MID) {
+      // active pair a = (k1 - crank KPO) kc + col; exclusive prefix of the flag counts by
+      // one warp (each lane a contiguous chunk), then every thread copies its pairs' entries
+      constexpr int KPO = SH / L1;
+      const int np = KPO * kc;
+      __syncthreads();
+      if (tid < 32) {
+        const int chunk = (np + 31) / 32, lo = min(np, tid * chunk), hi = min(np, lo + chunk);
+        int sum = 0;
+        for (int q = lo; q < hi; ++q) sum += __popc(pmask[(q / kc) * L1 + q % kc]);
+        int incl = sum;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const int o = __shfl_up_sync(0xffffffffu, incl, d);
+          if (tid >= d) incl += o;
+        }
+        int run = incl - sum;
+        for (int q = lo; q < hi; ++q) {
+          poff[q] = (uint16_t)run;
+          run += __popc(pmask[(q / kc) * L1 + q % kc]);
+        }
+      }
+      __syncthreads();
+      for (int q = tid; q < np; q += T) {
+        const int pl = (q / kc) * L1 + q % kc;
+        const int k1 = crank * KPO + q / kc, col = q % kc;
+        uint32_t pm = pmask[pl];
+        int idx = poff[q];
+        while (pm && idx < S::MCAP) {
+          const int fq = __ffs(pm) - 1;
+          pm &= pm - 1;
+          const int f = (k1 + RP * fq) * L1 + col;
+          const float2 b = bt ? bt[f] : make_float2(0.f, 0.f);
+          mtab[idx++] = make_float4(mult[f], b.x, b.y, 0.f);
+        }
+      }
     }
   }
 
@@ -436,18 +501,15 @@ struct FusedCta {
     for (int i = 0; i < 4; ++i) a[i] = out[i];
   }
 
-  __device__ __forceinline__ void middle_split(const uint32_t* peer, const float* mult_g, const float2* bt_g,
-                                               int kc) {
+  // Lane e of active pair a = (k1 - crank KPO) kc + col: load(i) returns group e + 4 i of the
+  // pair after the local column DFT, store(i, x) takes the same group's inverse result.
+  template <typename Load, typename Store>
+  __device__ __forceinline__ void middle_lanes(const float* mult_g, const float2* bt_g, int kc, Load&& load,
+                                               Store&& store) {
     constexpr int KPO = SH / L1;  // frequencies k1 owned by this CTA, all columns each
     const int np = KPO * kc;     // active pairs
     const int lane = tid & 31, e = tid & 3;
     const int rounds = (4 * np + T - 1) / T;
-    // shared::cluster base of the CTA holding each of this lane's groups e + 4 i
-    uint32_t base[4];
-    const uint32_t w = smem_addr(work);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) base[i] = cluster_map(w, (e + 4 * i) % C);
-    (void)peer;
     for (int rd = 0; rd < rounds; ++rd) {
       const int t = rd * T + tid;
       const bool on = t < 4 * np;
@@ -455,12 +517,12 @@ struct FusedCta {
       const int k1 = crank * KPO + a / kc, col = a % kc;
       const int pl = (k1 - crank * KPO) * L1 + col;
       const uint32_t pm = on ? pmask[pl] : 0u;
+      const int pbase = on ? (int)poff[a] : 0;
       float2 v[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int g = e + 4 * i;
-        const int off = ((g / C) + QV * k1) * P + pad16(col);
-        v[i] = pm ? ld_cluster(base[i] + off * 8) : make_float2(0.f, 0.f);
+        v[i] = pm ? load(a, k1, col, i) : make_float2(0.f, 0.f);
         if (g) v[i] = twmul<false>(v[i], tw[g * k1 * (NMAX / L2)]);
       }
       dft4<false>(v[0], v[1], v[2], v[3]);
@@ -472,9 +534,18 @@ struct FusedCta {
       for (int kk = 0; kk < 4; ++kk) {
         const int q = e + 4 * kk;
         if (pm & (1u << q)) {
-          const int f = (k1 + RP * q) * L1 + col;
-          const float m = ld_ro_f32(&mult_g[f]);
-          const float2 b = bt_g ? ld_ro_f32x2(&bt_g[f]) : make_float2(0.f, 0.f);
+          const int idx = pbase + __popc(pm & ((1u << q) - 1u));
+          float m;
+          float2 b;
+          if (idx < S::MCAP) {
+            const float4 t4 = mtab[idx];
+            m = t4.x;
+            b = make_float2(t4.y, t4.z);
+          } else {
+            const int f = (k1 + RP * q) * L1 + col;
+            m = ld_ro_f32(&mult_g[f]);
+            b = bt_g ? ld_ro_f32x2(&bt_g[f]) : make_float2(0.f, 0.f);
+          }
           v[kk] = make_float2(v[kk].x * m - b.x, v[kk].y * m - b.y);
         } else {
           v[kk] = make_float2(0.f, 0.f);
@@ -491,19 +562,36 @@ struct FusedCta {
           const int g = e + 4 * i;
           float2 o = v[i];
           if (g) o = twmul<true>(o, tw[g * k1 * (NMAX / L2)]);
-          const int off = ((g / C) + QV * k1) * P + pad16(col);
-          st_cluster(base[i] + off * 8, o);
+          store(k1, col, i, o);
         }
       }
     }
   }
 
-  // ---------------------------------------------------------------------------------------
-  // cross-group radix-Q stage, Fourier-domain update, inverse radix-Q stage (in place)
+  // pull form: every group is read from and written back to the CTA that holds it
+  __device__ __forceinline__ void middle_split(const float* mult_g, const float2* bt_g, int kc) {
+    const int e = tid & 3;
+    // shared::cluster base of the CTA holding each of this lane's groups e + 4 i
+    uint32_t base[4];
+    const uint32_t w = smem_addr(work);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) base[i] = cluster_map(w, (e + 4 * i) % C);
+    middle_lanes(
+        mult_g, bt_g, kc,
+        [&](int, int k1, int col, int i) {
+          const int g = e + 4 * i;
+          return ld_cluster(base[i] + (((g / C) + QV * k1) * P + pad16(col)) * 8);
+        },
+        [&](int k1, int col, int i, float2 o) {
+          const int g = e + 4 * i;
+          st_cluster(base[i] + (((g / C) + QV * k1) * P + pad16(col)) * 8, o);
+        });
+  }
+
   // ---------------------------------------------------------------------------------------
   __device__ __forceinline__ void middle(const uint32_t* peer, const float* mult_g, const float2* bt_g, int kc) {
     if constexpr (S::SPLIT_MID) {
-      middle_split(peer, mult_g, bt_g, kc);
+      middle_split(mult_g, bt_g, kc);
       return;
     }
     constexpr int PT = (SH + T - 1) / T;
@@ -604,7 +692,6 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
     fused_solve_kernel(const FusedArgs a) {
   using S = FusedShape<L1, L2, ADMM, TILE>;
   constexpr int C = S::C, E = S::E, T = S::T, P = S::P, NMAX = S::NMAX, R = S::R;
-  constexpr int Q = S::Q, RP = S::RP, SH = S::SH;
 
   extern __shared__ float4 smem_raw[];
   FusedCta<S> cta;
@@ -622,6 +709,10 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
   cta.tw256 = reinterpret_cast<float2*>(sp);
   sp += 256 * 8;
   cta.tw16 = reinterpret_cast<float2*>(sp);
+  sp += 16 * 8;
+  cta.mtab = reinterpret_cast<float4*>(sp);
+  sp += S::MCAP * 16;
+  cta.poff = reinterpret_cast<uint16_t*>(sp);
   cta.tid = threadIdx.x;
   int crank = 0;
   if constexpr (C > 1) crank = (int)cg::this_cluster().block_rank();
@@ -647,7 +738,7 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
   }
 
   // ---- load twiddles, the frequency masks and the initial state
-  cta.load_tables(a.twiddle, mult, bt);
+  cta.load_tables(a.twiddle, mult, bt, kc);
   for (int idx = threadIdx.x; idx < E; idx += T) {
     const int s = idx / L1, e = idx % L1;
     const int gidx = (crank + C * s) * L1 + e;
@@ -725,12 +816,12 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
       cluster_barrier<C>();
       cta.template col_dft<true>(kc);
       __syncthreads();
-      cta.sq_inv1(nz);
+      if (nz > 2) cta.sq_inv1(nz);
       float sc, kap;
       float2* save_t;
       layer(it, sc, kap, save_t);
       cta.sq_inv2_epi_fwd1(
-          [&](int row, int e, float2 g) { return update(row, e, g, beta, last, sc, kap, save_t); }, !last);
+          [&](int row, int e, float2 g) { return update(row, e, g, beta, last, sc, kap, save_t); }, !last, nz);
     }
   } else {
     for (int it = 0; it < a.iters; ++it) {
