@@ -9,6 +9,9 @@ matrix D_s = Psi (D2 kron D1) is formed explicitly in complex128 and every Gram
 product is two dense matrix-vector products (Section II-B).  No FFT is used
 anywhere in it; the FFT identity of Section III-B is what the CUDA path relies on
 and what the tests check the two against.
+
+``oracle.peaks`` holds the post-processing step of Section II-A: peak picking on
+|c| and the map from harmonic pairs to the angles (phi, theta).
 """
 from .lasso import (  # noqa: F401
     dictionary,
@@ -32,3 +35,4 @@ from .lasso import (  # noqa: F401
     unrolled_forward,
     unrolled_backward,
 )
+from . import peaks  # noqa: F401
