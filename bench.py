@@ -409,6 +409,39 @@ def run_workload(args):
                 "nnz_fp32": int(np.count_nonzero(c32)), "nnz_fp64": int(np.count_nonzero(c64)),
                 "kkt_fp32": float(r32["kkt"][0]), "kkt_fp64": float(r64["kkt"][0]),
                 "objective_fp32": float(r32["objective"][0]), "objective_fp64": float(r64["objective"][0])}
+    elif args.workload == "peaks":
+        # harmonic / angle extraction (Section II-A) on the solutions of the batched 256x256 workload
+        B, T, K = args.batch, args.iters, 16
+        snaps = make_batch(B, 0)
+        insts = [dict(M1=s.M1, M2=s.M2, L1=s.L1, L2=s.L2, mask=s.mask, y=s.y, lam=WORKLOAD["lam_frac"],
+                      lam_is_frac=True) for s in snaps]
+        stream = torch.cuda.Stream()
+        solver = bccb.BatchSolver(insts, "fista", stream=stream)
+        y = torch.from_numpy(solver.y_host).cuda()
+        c = torch.zeros(solver.total_c, dtype=torch.complex64, device="cuda")
+        solver.solve(y, T, c, check=False)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            out = solver.peaks(c, K, 0.05)  # warm-up
+            ev0.record(stream)
+            for _ in range(5):
+                out = solver.peaks(c, K, 0.05)
+            ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / 5
+        cnt = out["count"].cpu().numpy()
+        c_host = c[: 16 * 65536].cpu().numpy()
+        t0 = time.perf_counter()
+        for i in range(16):
+            oracle.peaks.peaks(c_host[i * 65536:(i + 1) * 65536].reshape(256, 256), K, 0.05)
+        cpu_s = (time.perf_counter() - t0) / 16
+        solver.close()
+        line = {"workload": f"peak extraction and harmonic-to-angle map, K={K}, rel_thresh=0.05, on the {T}-iteration "
+                            f"FISTA solutions of {B} 256x256 snapshots", "value": B / (ms / 1e3),
+                "unit": "instances/s", "ms_per_batch": ms, "peaks_per_instance_median": float(np.median(cnt)),
+                "bytes_read_per_instance_pass": 65536 * 8,
+                "cpu_oracle": {"ms_per_instance": cpu_s * 1e3, "cores": 1, "sample": "16 instances"}}
     elif args.workload == "single64":
         s = synth.config_snapshot(1, 0)
         inst = [dict(M1=s.M1, M2=s.M2, L1=s.L1, L2=s.L2, mask=s.mask, y=s.y, lam=0.1, lam_is_frac=True)]
@@ -466,7 +499,7 @@ def main():
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-1e-4 measurement")
     ap.add_argument("--tune-cache", default=None, help="autotuner cache file (default: measure every run)")
     ap.add_argument("--workload", default="batched256",
-                    choices=["batched256", "ragged", "precision1024", "single64", "table1"],
+                    choices=["batched256", "ragged", "precision1024", "single64", "table1", "peaks"],
                     help="batched256 is the benchmark metric; the others print their own line")
     ap.add_argument("--trials", type=int, default=3, help="trials per Table I cell (--workload table1)")
     ap.add_argument("--traffic-bytes", type=float, default=None,

@@ -179,6 +179,27 @@ int bccb_unrolled_bwd(bccb_solver_t s, int layers, const float* scale_dev, const
 int bccb_set_timing(bccb_solver_t s, int enable);
 int bccb_last_timing(bccb_solver_t s, float* setup_ms, float* iterate_ms, float* check_ms, int64_t* launches);
 
+/* Harmonic and angle estimates from a solution (Section II-A): the support of c
+ * marks harmonic pairs (f1, f2) = (-1/2 + l1/L1, -1/2 + l2/L2), and each pair gives
+ * the angles through f1 = g cos(phi) sin(theta), f2 = g sin(phi) sin(theta) with the
+ * half-wavelength spacing g = 1/2.  The paper gives no peak-picking rule; this one:
+ *   m(p) = |c(p)|^2 in c's precision (x*x and y*y rounded, then their sum);
+ *   p is a peak when m(p) > 0, m(p) >= rel_thresh^2 * max m, and for each of its 8
+ *   cyclic neighbours q: m(p) > m(q), or m(p) == m(q) and p < q (index l1 + l2 L1);
+ *   peaks rank by m descending, then index ascending; the first K are returned.
+ * c_dev: a solution packed like c_out (complex64, or complex128 for a BCCB_F64
+ * solver).  Outputs (device, instance i at [i*K, (i+1)*K), caller-owned):
+ *   idx_dev  int32   l1 + l2 L1, -1 past the instance's peak count;
+ *   mag_dev  float64 |c| = sqrt(m) in c's precision (0 past the count);
+ *   harm_dev float64 pairs (f1, f2);
+ *   ang_dev  float64 pairs (phi, theta), phi = atan2(2 f2, 2 f1) in [-pi, pi],
+ *            theta = asin(sqrt((2 f1)^2 + (2 f2)^2)); NaN where that sum exceeds 1
+ *            (outside the visible region) and past the count;
+ *   count_dev int32 per instance, nullable: the number of peaks before the cut to K.
+ * K in [1, 1024], rel_thresh in [0, 1], else INVALID_ARG.  Asynchronous. */
+int bccb_batch_peaks(bccb_solver_t s, const void* c_dev, int K, double rel_thresh, int32_t* idx_dev,
+                     double* mag_dev, double* harm_dev, double* ang_dev, int32_t* count_dev);
+
 /* Number of instances, and the (L1, L2, N) of instance i. */
 int bccb_batch_size(bccb_solver_t s, int* n);
 int bccb_instance_shape(bccb_solver_t s, int i, int* L1, int* L2, int* N);

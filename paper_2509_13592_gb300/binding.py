@@ -62,6 +62,7 @@ def _load():
     lib.bccb_batch_tile.argtypes = [vp, i32, i32, P(i32)]
     lib.bccb_unrolled_fwd.argtypes = [vp, vp, i32, vp, vp, vp, vp, i32]
     lib.bccb_unrolled_bwd.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp]
+    lib.bccb_batch_peaks.argtypes = [vp, vp, i32, dbl, vp, vp, vp, vp, vp]
     lib.bccb_batch_size.argtypes = [vp, P(i32)]
     lib.bccb_instance_shape.argtypes = [vp, i32, P(i32), P(i32), P(i32)]
     lib.bccb_destroy.argtypes = [vp]
@@ -72,7 +73,7 @@ def _load():
     for name in ("bccb_batch_create", "bccb_batch_create2", "bccb_batch_solve", "bccb_batch_solve_host", "bccb_batch_results",
                  "bccb_batch_get", "bccb_create", "bccb_solve", "bccb_batch_size", "bccb_instance_shape",
                  "bccb_destroy", "bccb_set_timing", "bccb_last_timing", "bccb_batch_capture", "bccb_batch_replay",
-                 "bccb_batch_tune", "bccb_batch_tile", "bccb_unrolled_fwd", "bccb_unrolled_bwd"):
+                 "bccb_batch_tune", "bccb_batch_tile", "bccb_unrolled_fwd", "bccb_unrolled_bwd", "bccb_batch_peaks"):
         getattr(lib, name).restype = i32
     return lib
 
@@ -200,6 +201,12 @@ def bccb_unrolled_bwd(h: int, layers: int, scale_dev, thresh_dev, saved_dev, gra
                                   _ptr(grad_c_dev), _ptr(grad_scale_dev), _ptr(grad_thresh_dev)), h)
 
 
+def bccb_batch_peaks(h: int, c_dev, K: int, rel_thresh: float, idx_dev, mag_dev, harm_dev, ang_dev,
+                     count_dev=None) -> None:
+    _raise(_lib.bccb_batch_peaks(h, _ptr(c_dev), int(K), float(rel_thresh), _ptr(idx_dev), _ptr(mag_dev),
+                                 _ptr(harm_dev), _ptr(ang_dev), _ptr(count_dev)), h)
+
+
 def bccb_set_timing(h: int, enable: bool) -> None:
     _raise(_lib.bccb_set_timing(h, 1 if enable else 0), h)
 
@@ -275,6 +282,20 @@ class BatchSolver:
 
     def results(self):
         return bccb_batch_results(self.handle, self.n)
+
+    def peaks(self, c_dev, K: int, rel_thresh: float = 0.0):
+        """Top-K peaks of every instance (bccb_batch_peaks); device tensors
+        idx (n, K) int32, mag (n, K), harm (n, K, 2), ang (n, K, 2) float64, count (n,) int32."""
+        import torch
+
+        dev = c_dev.device
+        idx = torch.empty((self.n, K), dtype=torch.int32, device=dev)
+        mag = torch.empty((self.n, K), dtype=torch.float64, device=dev)
+        harm = torch.empty((self.n, K, 2), dtype=torch.float64, device=dev)
+        ang = torch.empty((self.n, K, 2), dtype=torch.float64, device=dev)
+        count = torch.empty((self.n,), dtype=torch.int32, device=dev)
+        bccb_batch_peaks(self.handle, c_dev, K, rel_thresh, idx, mag, harm, ang, count)
+        return dict(idx=idx, mag=mag, harm=harm, ang=ang, count=count)
 
     def get(self, what, dst_dev):
         bccb_batch_get(self.handle, what, dst_dev)

@@ -615,6 +615,17 @@ int bccb_unrolled_bwd(bccb_solver_t s, int layers, const float* scale_dev, const
   return BCCB_OK;
 }
 
+int bccb_batch_peaks(bccb_solver_t s, const void* c_dev, int K, double rel_thresh, int32_t* idx_dev,
+                     double* mag_dev, double* harm_dev, double* ang_dev, int32_t* count_dev) {
+  if (!s) return fail(nullptr, BCCB_ERR_INVALID_ARG, "solver is NULL");
+  if (!c_dev || !idx_dev || !mag_dev || !harm_dev || !ang_dev) return fail(s, BCCB_ERR_INVALID_ARG, "NULL buffer");
+  if (K < 1 || K > bccb::kMaxPeakK) return fail(s, BCCB_ERR_INVALID_ARG, "K outside [1, 1024]");
+  if (!(rel_thresh >= 0.0 && rel_thresh <= 1.0)) return fail(s, BCCB_ERR_INVALID_ARG, "rel_thresh outside [0, 1]");
+  BCCB_CUDA(s, cudaSetDevice(s->device));
+  BCCB_CUDA(s, bccb::run_peaks(s, c_dev, K, rel_thresh, idx_dev, mag_dev, harm_dev, ang_dev, count_dev));
+  return BCCB_OK;
+}
+
 int bccb_batch_tile(bccb_solver_t s, int L1, int L2, int* tile) {
   if (!s || !tile) return fail(s, BCCB_ERR_INVALID_ARG, "NULL argument");
   *tile = 0;

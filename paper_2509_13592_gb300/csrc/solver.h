@@ -117,4 +117,8 @@ const FusedEntry* fused_lookup(int L1, int L2, bool admm, int tile = 0);
 const AdjointEntry* adjoint_lookup(int L1, int L2);
 // the unrolled network's forward kernel (square grids L1 = L2, FISTA, default tile)
 const FusedEntry* learned_lookup(int L1, int L2);
+// peaks.cu: top-K peaks of every instance of c and their harmonics and angles
+constexpr int kMaxPeakK = 1024;
+cudaError_t run_peaks(bccb_solver* s, const void* c_dev, int K, double rel_thresh, int* idx, double* mag,
+                      double* harm, double* ang, int* count);
 }  // namespace bccb
