@@ -348,9 +348,11 @@ def run_gpu(args, rank, world, local_rank):
 # ------------------------------------------------------------------------------------------
 
 
-def _solve_timed(bccb, torch, insts, algo, iters, rho=1.0, prec="f32", reps=3, check=False):
+def _solve_timed(bccb, torch, insts, algo, iters, rho=1.0, prec="f32", reps=3, check=False, method="fft"):
     stream = torch.cuda.Stream()
     solver = bccb.BatchSolver(insts, algo, rho, stream=stream, prec=prec)
+    if method != "fft":
+        solver.set_method(method)
     cdt = torch.complex128 if prec == "f64" else torch.complex64
     y = torch.from_numpy(solver.y_host).cuda()
     c = torch.zeros(solver.total_c, dtype=cdt, device="cuda")
@@ -454,7 +456,7 @@ def run_workload(args):
         for algo in ("ista", "fista", "admm"):
             for L1 in (64, 128, 256, 512):
                 for it in (50, 100, 200, 400):
-                    errs, errs32, t_reg, t_gpu = [], [], [], []
+                    errs, errs32, t_reg, t_gpu, t_dense, t_fast_it, eps_dense, dense_gbs = ([] for _ in range(8))
                     for trial in range(args.trials):
                         s = synth.paper_experiment_snapshot(trial, L1)
                         A = oracle.dictionary(s.mask, s.M1, s.M2, s.L1, s.L2)
@@ -471,13 +473,26 @@ def run_workload(args):
                         (c64, _), t64, _ = _solve_timed(bccb, torch, inst, algo, it, rho=float(s.N), prec="f64",
                                                         reps=1)
                         (c32, _), t32, _ = _solve_timed(bccb, torch, inst, algo, it, rho=float(s.N), reps=1)
+                        (cd, _), td, _ = _solve_timed(bccb, torch, inst, algo, it, rho=float(s.N), reps=1,
+                                                      method="dense")
                         nr = np.linalg.norm(ref)
                         errs.append(float(np.linalg.norm(c64 - ref) / nr) if nr else 0.0)
                         errs32.append(float(np.linalg.norm(c32 - ref) / nr) if nr else 0.0)
+                        nd = np.linalg.norm(cd)
+                        eps_dense.append(float(np.linalg.norm(cd - c32) / nd) if nd else 0.0)
                         t_gpu.append(t32["ms"])
+                        t_fast_it.append(t32["iterate_ms"])
+                        t_dense.append(td["iterate_ms"])
+                        L = L1 * 32
+                        dense_gbs.append(8.0 * L * L * it / (td["iterate_ms"] / 1e3) / 1e9)
                     rows.append({"algo": algo, "L1": L1, "n_iter": it, "eps_r_fp64_gpu": float(np.mean(errs)),
                                  "eps_r_fp32_gpu": float(np.mean(errs32)), "t_reg_cpu_ms": float(np.mean(t_reg)),
-                                 "t_fast_gpu_ms": float(np.mean(t_gpu))})
+                                 "t_fast_gpu_ms": float(np.mean(t_gpu)),
+                                 "t_reg_gpu_iter_ms": float(np.mean(t_dense)),
+                                 "t_fast_gpu_iter_ms": float(np.mean(t_fast_it)),
+                                 "t_reg_over_t_fast_gpu": float(np.mean(t_dense) / np.mean(t_fast_it)),
+                                 "eps_r_reg_vs_fast_fp32_gpu": float(np.mean(eps_dense)),
+                                 "dense_gram_gbs": float(np.mean(dense_gbs))})
         line = {"workload": f"paper experiment shape: M1=51, M2=16, N=40, L2=32, 15 dB, K in 1..10, "
                             f"{args.trials} trials; ADMM rho = N", "rows": rows, "cpu_cores": os.cpu_count()}
     else:

@@ -179,6 +179,26 @@ int bccb_unrolled_bwd(bccb_solver_t s, int layers, const float* scale_dev, const
 int bccb_set_timing(bccb_solver_t s, int enable);
 int bccb_last_timing(bccb_solver_t s, float* setup_ms, float* iterate_ms, float* check_ms, int64_t* launches);
 
+/* Iteration engine of a solver. */
+enum { BCCB_FFT = 0, BCCB_DENSE = 1 };
+
+/* Select how the iterations apply the Gram product.  BCCB_FFT (the default): the 2D
+ * FFT identity of eq:Rc (fused cluster kernel or multi-pass).  BCCB_DENSE: the
+ * paper's "regular" implementation, whose dominant term is the O(L^2) product with an
+ * L x L matrix (eq:ista, eq:fista, eq:admm): the Gram G = D_s^H D_s of every instance
+ * is built once from its definition (FP64, stored complex64, L^2 * 8 bytes per
+ * instance) and each iteration is one dense matrix-vector product plus the pointwise
+ * update, with the identity part applied exactly:
+ *   ISTA/FISTA  u = x - mu (G x) + mu b;
+ *   ADMM        c = w - (G w)/(rho + L) + b/(rho + L), w = z - v, from the Woodbury
+ *               form of (G + rho I)^{-1} with D_s D_s^H = L I.
+ * Setup (Lambda, mu, b, lam) and the FP64 check are those of the FFT engine, so the
+ * two engines differ only in the iterations.  Requirements: a BCCB_F32 solver; for
+ * ADMM every M_i <= L_i; at most 64 GiB of matrices in total; else UNSUPPORTED.
+ * Switching to BCCB_DENSE builds the matrices and synchronises; switching back frees
+ * them. */
+int bccb_batch_set_method(bccb_solver_t s, int method);
+
 /* Harmonic and angle estimates from a solution (Section II-A): the support of c
  * marks harmonic pairs (f1, f2) = (-1/2 + l1/L1, -1/2 + l2/L2), and each pair gives
  * the angles through f1 = g cos(phi) sin(theta), f2 = g sin(phi) sin(theta) with the

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libbccb.so")
 
 ISTA, FISTA, ADMM = 0, 1, 2
 F32, F64 = 0, 1
+FFT, DENSE = 0, 1
 ALGOS = {"ista": ISTA, "fista": FISTA, "admm": ADMM}
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_KKT, ERR_TIMEOUT = range(6)
 GET_LAMBDA, GET_B, GET_MULT, GET_CTERM = 0, 1, 2, 3
@@ -63,6 +64,7 @@ def _load():
     lib.bccb_unrolled_fwd.argtypes = [vp, vp, i32, vp, vp, vp, vp, i32]
     lib.bccb_unrolled_bwd.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp]
     lib.bccb_batch_peaks.argtypes = [vp, vp, i32, dbl, vp, vp, vp, vp, vp]
+    lib.bccb_batch_set_method.argtypes = [vp, i32]
     lib.bccb_batch_size.argtypes = [vp, P(i32)]
     lib.bccb_instance_shape.argtypes = [vp, i32, P(i32), P(i32), P(i32)]
     lib.bccb_destroy.argtypes = [vp]
@@ -73,7 +75,8 @@ def _load():
     for name in ("bccb_batch_create", "bccb_batch_create2", "bccb_batch_solve", "bccb_batch_solve_host", "bccb_batch_results",
                  "bccb_batch_get", "bccb_create", "bccb_solve", "bccb_batch_size", "bccb_instance_shape",
                  "bccb_destroy", "bccb_set_timing", "bccb_last_timing", "bccb_batch_capture", "bccb_batch_replay",
-                 "bccb_batch_tune", "bccb_batch_tile", "bccb_unrolled_fwd", "bccb_unrolled_bwd", "bccb_batch_peaks"):
+                 "bccb_batch_tune", "bccb_batch_tile", "bccb_unrolled_fwd", "bccb_unrolled_bwd", "bccb_batch_peaks",
+                 "bccb_batch_set_method"):
         getattr(lib, name).restype = i32
     return lib
 
@@ -201,6 +204,11 @@ def bccb_unrolled_bwd(h: int, layers: int, scale_dev, thresh_dev, saved_dev, gra
                                   _ptr(grad_c_dev), _ptr(grad_scale_dev), _ptr(grad_thresh_dev)), h)
 
 
+def bccb_batch_set_method(h: int, method) -> None:
+    m = {"fft": FFT, "dense": DENSE}[method] if isinstance(method, str) else int(method)
+    _raise(_lib.bccb_batch_set_method(h, m), h)
+
+
 def bccb_batch_peaks(h: int, c_dev, K: int, rel_thresh: float, idx_dev, mag_dev, harm_dev, ang_dev,
                      count_dev=None) -> None:
     _raise(_lib.bccb_batch_peaks(h, _ptr(c_dev), int(K), float(rel_thresh), _ptr(idx_dev), _ptr(mag_dev),
@@ -282,6 +290,10 @@ class BatchSolver:
 
     def results(self):
         return bccb_batch_results(self.handle, self.n)
+
+    def set_method(self, method):
+        """'fft' (default) or 'dense' (the stored L x L Gram, bccb_batch_set_method)."""
+        bccb_batch_set_method(self.handle, method)
 
     def peaks(self, c_dev, K: int, rel_thresh: float = 0.0):
         """Top-K peaks of every instance (bccb_batch_peaks); device tensors

@@ -24,6 +24,8 @@ thread_local std::string g_create_error;
 
 bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
+constexpr size_t kDenseMaxBytes = size_t(64) << 30;
+
 int fail(bccb_solver* s, int code, const std::string& msg) {
   if (s)
     s->last_error = msg;
@@ -67,8 +69,21 @@ void release_streams(bccb_solver* s) {
   s->d_probe = nullptr;
 }
 
+void release_dense(bccb_solver* s) {
+  void* ptrs[] = {s->d_gram, s->d_gram_off, s->d_dense_k, s->d_dense_s0, s->d_dense_s1, s->d_dense_x[0],
+                  s->d_dense_x[1]};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  s->d_gram = nullptr;
+  s->d_gram_off = nullptr;
+  s->d_dense_k = s->d_dense_s0 = s->d_dense_s1 = nullptr;
+  s->d_dense_x[0] = s->d_dense_x[1] = nullptr;
+  s->dense_bytes = 0;
+}
+
 void release(bccb_solver* s) {
   release_streams(s);
+  release_dense(s);
   void* ptrs[] = {s->d_desc,   s->d_mask_idx, s->d_lam64,   s->d_b64,     s->d_w64,     s->d_mult,
                   s->d_cterm,  s->d_par,      s->d_fused,   s->d_ids,     s->d_beta,    s->d_beta64,
                   s->d_kkt,    s->d_obj,      s->d_red,     s->d_tw32,    s->d_tw64,    s->d_y_stage,
@@ -285,6 +300,14 @@ int bccb_batch_solve(bccb_solver_t s, const void* y_dev, int iters, const void* 
   a.aux_out = (s->algo == BCCB_ADMM) ? reinterpret_cast<float2*>(aux_out_dev) : nullptr;
   a.iters = iters;
   a.pad_ = 0;
+  if (s->method == BCCB_DENSE) {
+    BCCB_CUDA(s, bccb::run_dense(s, iters, c0_dev, c_out_dev, s->algo == BCCB_ADMM ? aux_out_dev : nullptr));
+    if (s->timing) BCCB_CUDA(s, record_timing(s, 2));
+    if (check) BCCB_CUDA(s, bccb::run_check(s, y, c_out_dev));
+    if (s->timing) BCCB_CUDA(s, record_timing(s, 3));
+    s->last_checked = check != 0;
+    return BCCB_OK;
+  }
   auto launch_class = [&](const bccb::ShapeClass& c, cudaStream_t st) -> cudaError_t {
     if (c.multipass)
       return bccb::run_multipass(s, s->d_ids + c.first, c.count, iters, c0_dev, c_out_dev,
@@ -612,6 +635,34 @@ int bccb_unrolled_bwd(bccb_solver_t s, int layers, const float* scale_dev, const
     a.ids = s->d_ids + c.first;
     BCCB_CUDA(s, ae->launch(a, c.count, s->stream));
   }
+  return BCCB_OK;
+}
+
+int bccb_batch_set_method(bccb_solver_t s, int method) {
+  if (!s) return fail(nullptr, BCCB_ERR_INVALID_ARG, "solver is NULL");
+  if (method != BCCB_FFT && method != BCCB_DENSE) return fail(s, BCCB_ERR_INVALID_ARG, "unknown method");
+  BCCB_CUDA(s, cudaSetDevice(s->device));
+  if (method == s->method) return BCCB_OK;
+  if (method == BCCB_FFT) {
+    BCCB_CUDA(s, cudaStreamSynchronize(s->stream));
+    release_dense(s);
+    s->method = BCCB_FFT;
+    return BCCB_OK;
+  }
+  if (s->prec != BCCB_F32) return fail(s, BCCB_ERR_UNSUPPORTED, "the dense method runs in complex64 only");
+  size_t bytes = 0;
+  for (const InstDesc& d : s->h_desc) {
+    if (s->algo == BCCB_ADMM && (d.M1 > d.L1 || d.M2 > d.L2))
+      return fail(s, BCCB_ERR_UNSUPPORTED, "dense ADMM needs M_i <= L_i (no fold: D D^H = L I)");
+    bytes += sizeof(float2) * (size_t)d.L1 * d.L2 * (size_t)d.L1 * d.L2;
+  }
+  if (bytes > kDenseMaxBytes) return fail(s, BCCB_ERR_UNSUPPORTED, "dense Gram matrices exceed 64 GiB");
+  const cudaError_t e = bccb::dense_prepare(s);
+  if (e != cudaSuccess) {
+    release_dense(s);
+    return fail(s, BCCB_ERR_CUDA, std::string("dense_prepare: ") + cudaGetErrorString(e));
+  }
+  s->method = BCCB_DENSE;
   return BCCB_OK;
 }
 

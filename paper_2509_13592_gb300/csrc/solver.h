@@ -97,6 +97,15 @@ struct bccb_solver {
   void* d_mp_work = nullptr;
   void* d_mp_s0 = nullptr;
   void* d_mp_s1 = nullptr;
+  // iteration engine: 0 = FFT (fused / multi-pass), 1 = dense L x L Gram (dense.cu)
+  int method = 0;
+  float2* d_gram = nullptr;       // per instance L x L complex64, row-major
+  int64_t* d_gram_off = nullptr;  // element offset of each instance's block
+  float2* d_dense_k = nullptr;    // constant term per cell
+  float2* d_dense_s0 = nullptr;   // c (ISTA/FISTA) or z (ADMM)
+  float2* d_dense_s1 = nullptr;   // v (ADMM)
+  float2* d_dense_x[2] = {nullptr, nullptr};  // double-buffered product input
+  size_t dense_bytes = 0;
 };
 
 namespace bccb {
@@ -117,6 +126,9 @@ const FusedEntry* fused_lookup(int L1, int L2, bool admm, int tile = 0);
 const AdjointEntry* adjoint_lookup(int L1, int L2);
 // the unrolled network's forward kernel (square grids L1 = L2, FISTA, default tile)
 const FusedEntry* learned_lookup(int L1, int L2);
+// dense.cu: build the stored Gram matrices (synchronises) and run the dense iterations
+cudaError_t dense_prepare(bccb_solver* s);
+cudaError_t run_dense(bccb_solver* s, int iters, const void* c0, void* c_out, void* aux);
 // peaks.cu: top-K peaks of every instance of c and their harmonics and angles
 constexpr int kMaxPeakK = 1024;
 cudaError_t run_peaks(bccb_solver* s, const void* c_dev, int K, double rel_thresh, int* idx, double* mag,
