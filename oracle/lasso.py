@@ -35,9 +35,10 @@ import scipy.linalg
 # ------------------------------------------------------------------------------------------
 
 
-def harmonic_grid(L: int) -> np.ndarray:
-    """Uniform harmonic grid f_l = -gamma + l*2*gamma/L with gamma = 1/2 (eq:uniform_grid)."""
-    return -0.5 + np.arange(L, dtype=np.float64) / L
+def harmonic_grid(L: int, gamma: float = 0.5) -> np.ndarray:
+    """Uniform harmonic grid f_l = -gamma + l*2*gamma/L (eq:uniform_grid); gamma is the element
+    spacing in wavelengths (Section II-A), 1/2 for the BCCB case of Section III."""
+    return -gamma + np.arange(L, dtype=np.float64) * (2.0 * gamma / L)
 
 
 def element_positions(mask, M1: int):
@@ -46,18 +47,19 @@ def element_positions(mask, M1: int):
     return lin % M1, lin // M1
 
 
-def dictionary(mask, M1: int, M2: int, L1: int, L2: int) -> np.ndarray:
+def dictionary(mask, M1: int, M2: int, L1: int, L2: int, gamma1: float = 0.5, gamma2: float = 0.5) -> np.ndarray:
     """Row-subsampled dictionary D_s = Psi (D2 kron D1) in complex128, shape (N, L1*L2).
 
-    D_i(m, l) = exp(-j 2 pi f_{i,l} m) (eq:subdictionary); the row of D for
+    D_i(m, l) = exp(-j 2 pi f_{i,l} m) (eq:subdictionary) on the grids of eq:uniform_grid
+    with spacings gamma1, gamma2 (1/2: half-wavelength, the BCCB case); the row of D for
     element (m1, m2) is row m1 + m2*M1 of D2 kron D1, i.e. kron(D2[m2], D1[m1])
     (eq:forward_model, eq:sparse_forward_model).
     """
     m1, m2 = element_positions(mask, M1)
     if np.any(m1 >= M1) or np.any(m2 >= M2):
         raise ValueError("mask larger than M1*M2")
-    D1 = np.exp(-2j * np.pi * np.outer(np.arange(M1), harmonic_grid(L1)))
-    D2 = np.exp(-2j * np.pi * np.outer(np.arange(M2), harmonic_grid(L2)))
+    D1 = np.exp(-2j * np.pi * np.outer(np.arange(M1), harmonic_grid(L1, gamma1)))
+    D2 = np.exp(-2j * np.pi * np.outer(np.arange(M2), harmonic_grid(L2, gamma2)))
     A = np.empty((m1.size, L1 * L2), dtype=np.complex128)
     for n in range(m1.size):
         A[n] = np.kron(D2[m2[n]], D1[m1[n]])

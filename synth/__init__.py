@@ -24,7 +24,7 @@ call gives the same arrays on any machine.
 from __future__ import annotations
 
 import dataclasses
-from typing import List, Optional
+from typing import Tuple, List, Optional
 
 import numpy as np
 
@@ -54,6 +54,7 @@ class Snapshot:
     amps: np.ndarray  # complex128 (K,)
     snr_db: Optional[float]  # None = noiseless
     lam_frac: float = 0.1  # lambda = lam_frac * ||A^H y||_inf (applied by the caller)
+    gamma: Tuple[float, float] = (0.5, 0.5)  # element spacings in wavelengths (Section II-A)
 
     @property
     def N(self) -> int:
@@ -76,12 +77,14 @@ def element_positions(mask: np.ndarray, M1: int):
     return lin % M1, lin // M1
 
 
-def on_grid_frequencies(rng: np.random.Generator, L1: int, L2: int, K: int) -> np.ndarray:
-    """K distinct grid points f_{i,l} = -1/2 + l/L_i (eq:uniform_grid, gamma = 1/2)."""
+def on_grid_frequencies(rng: np.random.Generator, L1: int, L2: int, K: int,
+                        gamma: Tuple[float, float] = (0.5, 0.5)) -> np.ndarray:
+    """K distinct grid points f_{i,l} = -gamma_i + l 2 gamma_i / L_i (eq:uniform_grid)."""
     flat = rng.choice(L1 * L2, size=K, replace=False)
     l1 = flat % L1
     l2 = flat // L1
-    return np.stack([-0.5 + l1 / L1, -0.5 + l2 / L2], axis=1)
+    g1, g2 = gamma
+    return np.stack([-g1 + l1 * (2.0 * g1 / L1), -g2 + l2 * (2.0 * g2 / L2)], axis=1)
 
 
 def _response(m1: np.ndarray, m2: np.ndarray, freqs: np.ndarray, amps: np.ndarray) -> np.ndarray:
@@ -103,22 +106,28 @@ def make_snapshot(
     unit_amplitude: bool = False,
     mask: Optional[np.ndarray] = None,
     lam_frac: float = 0.1,
+    gamma: Tuple[float, float] = (0.5, 0.5),
 ) -> Snapshot:
     """Draw one snapshot: mask (unless given), K sources, amplitudes, noise.
 
     ``on_grid`` puts the sources on the recovery grid; otherwise the harmonics
-    are uniform on [-1/2, 1/2)^2.  ``unit_amplitude`` gives |c_k| = 1 with a
-    uniform phase; otherwise c_k ~ CN(0, 1).
+    are uniform on [-gamma_1, gamma_1) x [-gamma_2, gamma_2) (the range of
+    f* = (gamma_1 cos(phi) sin(theta), gamma_2 sin(phi) sin(theta)), Section II-A;
+    [-1/2, 1/2)^2 for half-wavelength spacing).  ``unit_amplitude`` gives
+    |c_k| = 1 with a uniform phase; otherwise c_k ~ CN(0, 1).
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     if mask is None:
         mask = make_mask(rng, M1, M2, N)
     else:
         mask = np.asarray(mask, dtype=np.uint8).reshape(-1).copy()
+    g1, g2 = gamma
     if on_grid:
-        freqs = on_grid_frequencies(rng, L1, L2, K)
-    else:
+        freqs = on_grid_frequencies(rng, L1, L2, K, gamma)
+    elif gamma == (0.5, 0.5):
         freqs = rng.uniform(-0.5, 0.5, size=(K, 2))
+    else:
+        freqs = rng.uniform(0.0, 1.0, size=(K, 2)) * np.array([2 * g1, 2 * g2]) - np.array([g1, g2])
     if unit_amplitude:
         amps = np.exp(2j * np.pi * rng.uniform(0.0, 1.0, size=K))
     else:
@@ -130,7 +139,8 @@ def make_snapshot(
         sigma2 = p_s / (10.0 ** (snr_db / 10.0))
         noise = (rng.standard_normal(y.size) + 1j * rng.standard_normal(y.size)) * np.sqrt(sigma2 / 2.0)
         y = y + noise
-    return Snapshot(M1, M2, L1, L2, mask, y.astype(np.complex128), freqs, amps, snr_db, lam_frac)
+    return Snapshot(M1, M2, L1, L2, mask, y.astype(np.complex128), freqs, amps, snr_db, lam_frac,
+                    (float(g1), float(g2)))
 
 
 # --------------------------------------------------------------------------------------------
