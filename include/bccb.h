@@ -91,6 +91,22 @@ int bccb_batch_create(bccb_solver_t* out, const bccb_inst_t* insts, int n, const
 int bccb_batch_create2(bccb_solver_t* out, const bccb_inst_t* insts, int n, const uint8_t* masks_host,
                        int algo, double rho, int prec, void* cuda_stream);
 
+/* bccb_batch_create2 for element spacings gamma1, gamma2 (in wavelengths, Section II-A)
+ * other than 1/2.  The harmonic grids are f_{i,l} = -gamma_i + l 2 gamma_i / L_i
+ * (eq:uniform_grid); the Gram A^H A is then block Toeplitz with Toeplitz blocks
+ * (Section III-A), and every product with it is the L1 x L2 block of a product with
+ * the 2L1 x 2L2 circulant embedding, so the same FFT2 iterations run on the embedded
+ * grid with the unknown held at 0 outside the block.  mu = 1/lambda_max(A A^H) comes
+ * from a power iteration (FP32, finished by an FP64 Rayleigh quotient), b = A^H y from
+ * its definition in FP64.  The caller's packing is unchanged (L1 x L2 per instance).
+ * Limits: ISTA or FISTA (ADMM's (G + rho I)^{-1} is not a product with the embedding:
+ * UNSUPPORTED); L_i powers of two in [16, 512]; 1 <= M_i <= L_i, M_i <= 512; at most
+ * 1024 elements per instance; gamma_i in (0, 2].  gamma1 = gamma2 = 1/2 is exactly
+ * bccb_batch_create2.  bccb_batch_get, the dense method and the unrolled network are
+ * UNSUPPORTED on such a solver. */
+int bccb_batch_create_gamma(bccb_solver_t* out, const bccb_inst_t* insts, int n, const uint8_t* masks_host,
+                            int algo, double rho, int prec, double gamma1, double gamma2, void* cuda_stream);
+
 /* Run the whole hot path for every instance on the solver's stream:
  *   setup (FP64): Lambda = FFT2 of the Gram's first column (eq:lambda),
  *                 mu = 1/max Lambda (eq:ista), b = A^H y, lam, and the FP32
@@ -200,9 +216,10 @@ enum { BCCB_FFT = 0, BCCB_DENSE = 1 };
 int bccb_batch_set_method(bccb_solver_t s, int method);
 
 /* Harmonic and angle estimates from a solution (Section II-A): the support of c
- * marks harmonic pairs (f1, f2) = (-1/2 + l1/L1, -1/2 + l2/L2), and each pair gives
- * the angles through f1 = g cos(phi) sin(theta), f2 = g sin(phi) sin(theta) with the
- * half-wavelength spacing g = 1/2.  The paper gives no peak-picking rule; this one:
+ * marks harmonic pairs (f1, f2) = (-g1 + l1 2 g1/L1, -g2 + l2 2 g2/L2), and each pair
+ * gives the angles through f1 = g1 cos(phi) sin(theta), f2 = g2 sin(phi) sin(theta),
+ * with the solver's element spacings g1, g2 (1/2 unless created by
+ * bccb_batch_create_gamma).  The paper gives no peak-picking rule; this one:
  *   m(p) = |c(p)|^2 in c's precision (x*x and y*y rounded, then their sum);
  *   p is a peak when m(p) > 0, m(p) >= rel_thresh^2 * max m, and for each of its 8
  *   cyclic neighbours q: m(p) > m(q), or m(p) == m(q) and p < q (index l1 + l2 L1);
@@ -212,8 +229,8 @@ int bccb_batch_set_method(bccb_solver_t s, int method);
  *   idx_dev  int32   l1 + l2 L1, -1 past the instance's peak count;
  *   mag_dev  float64 |c| = sqrt(m) in c's precision (0 past the count);
  *   harm_dev float64 pairs (f1, f2);
- *   ang_dev  float64 pairs (phi, theta), phi = atan2(2 f2, 2 f1) in [-pi, pi],
- *            theta = asin(sqrt((2 f1)^2 + (2 f2)^2)); NaN where that sum exceeds 1
+ *   ang_dev  float64 pairs (phi, theta), phi = atan2(f2/g2, f1/g1) in [-pi, pi],
+ *            theta = asin(sqrt((f1/g1)^2 + (f2/g2)^2)); NaN where that sum exceeds 1
  *            (outside the visible region) and past the count;
  *   count_dev int32 per instance, nullable: the number of peaks before the cut to K.
  * K in [1, 1024], rel_thresh in [0, 1], else INVALID_ARG.  Asynchronous. */

@@ -48,6 +48,7 @@ def _load():
     P = ctypes.POINTER
     lib.bccb_batch_create.argtypes = [P(vp), P(bccb_inst_t), i32, vp, i32, dbl, vp]
     lib.bccb_batch_create2.argtypes = [P(vp), P(bccb_inst_t), i32, vp, i32, dbl, i32, vp]
+    lib.bccb_batch_create_gamma.argtypes = [P(vp), P(bccb_inst_t), i32, vp, i32, dbl, i32, dbl, dbl, vp]
     lib.bccb_batch_solve.argtypes = [vp, vp, i32, vp, vp, vp, i32]
     lib.bccb_batch_solve_host.argtypes = [vp, vp, i32, vp, i32]
     lib.bccb_batch_results.argtypes = [vp, vp, vp, vp, vp]
@@ -76,7 +77,7 @@ def _load():
                  "bccb_batch_get", "bccb_create", "bccb_solve", "bccb_batch_size", "bccb_instance_shape",
                  "bccb_destroy", "bccb_set_timing", "bccb_last_timing", "bccb_batch_capture", "bccb_batch_replay",
                  "bccb_batch_tune", "bccb_batch_tile", "bccb_unrolled_fwd", "bccb_unrolled_bwd", "bccb_batch_peaks",
-                 "bccb_batch_set_method"):
+                 "bccb_batch_set_method", "bccb_batch_create_gamma"):
         getattr(lib, name).restype = i32
     return lib
 
@@ -116,12 +117,13 @@ def _stream(stream) -> Optional[int]:
 
 
 def bccb_batch_create(insts: Sequence[bccb_inst_t], masks_host: np.ndarray, algo: int, rho: float = 1.0,
-                      stream=None, prec: int = F32) -> int:
+                      stream=None, prec: int = F32, gamma=(0.5, 0.5)) -> int:
     arr = (bccb_inst_t * len(insts))(*insts)
     masks = np.ascontiguousarray(masks_host, dtype=np.uint8)
     h = ctypes.c_void_p()
-    st = _lib.bccb_batch_create2(ctypes.byref(h), arr, len(insts), masks.ctypes.data_as(ctypes.c_void_p),
-                                 int(algo), float(rho), int(prec), _stream(stream))
+    st = _lib.bccb_batch_create_gamma(ctypes.byref(h), arr, len(insts), masks.ctypes.data_as(ctypes.c_void_p),
+                                      int(algo), float(rho), int(prec), float(gamma[0]), float(gamma[1]),
+                                      _stream(stream))
     _raise(st, None)
     return h.value
 
@@ -271,14 +273,14 @@ def pack(instances, dtype=np.complex64):
 class BatchSolver:
     """Owns one solver handle.  ``instances`` as for :func:`pack`."""
 
-    def __init__(self, instances, algo="fista", rho: float = 1.0, stream=None, prec="f32"):
+    def __init__(self, instances, algo="fista", rho: float = 1.0, stream=None, prec="f32", gamma=(0.5, 0.5)):
         self.algo = ALGOS[algo] if isinstance(algo, str) else int(algo)
         self.prec = {"f32": F32, "f64": F64}[prec] if isinstance(prec, str) else int(prec)
         self.dtype = np.complex128 if self.prec == F64 else np.complex64
         self.insts, self.masks, self.y_host, self.total_c = pack(instances, self.dtype)
         self.n = len(self.insts)
         self.offsets = [(q.c_off, q.L1, q.L2) for q in self.insts]
-        self.handle = bccb_batch_create(self.insts, self.masks, self.algo, rho, stream, self.prec)
+        self.handle = bccb_batch_create(self.insts, self.masks, self.algo, rho, stream, self.prec, gamma)
 
     def solve(self, y_dev, iters, c_out, c0=None, aux_out=None, check=True):
         bccb_batch_solve(self.handle, y_dev, iters, c0, c_out, aux_out, check)

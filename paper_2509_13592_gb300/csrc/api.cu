@@ -87,7 +87,8 @@ void release(bccb_solver* s) {
   void* ptrs[] = {s->d_desc,   s->d_mask_idx, s->d_lam64,   s->d_b64,     s->d_w64,     s->d_mult,
                   s->d_cterm,  s->d_par,      s->d_fused,   s->d_ids,     s->d_beta,    s->d_beta64,
                   s->d_kkt,    s->d_obj,      s->d_red,     s->d_tw32,    s->d_tw64,    s->d_y_stage,
-                  s->d_c_stage, s->d_mult64,  s->d_bt64,    s->d_mp_work, s->d_mp_s0,   s->d_mp_s1};
+                  s->d_c_stage, s->d_mult64,  s->d_bt64,    s->d_mp_work, s->d_mp_s0,   s->d_mp_s1,
+                  s->d_cint,   s->d_c0int,    s->d_toep_h,  s->d_toep_fb};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -115,8 +116,15 @@ int bccb_batch_create(bccb_solver_t* out, const bccb_inst_t* insts, int n, const
   return bccb_batch_create2(out, insts, n, masks_host, algo, rho, BCCB_F32, cuda_stream);
 }
 
-int bccb_batch_create2(bccb_solver_t* out, const bccb_inst_t* insts, int n, const uint8_t* masks_host, int algo,
-                       double rho, int prec, void* cuda_stream) {
+}  // extern "C"
+
+namespace {
+
+// blk (2 per instance, nullable): the caller's block bL1, bL2 of a circulant embedding whose
+// embedded size the instance table gives; uoff (nullable): the caller's solution offsets
+int create_impl(bccb_solver_t* out, const bccb_inst_t* insts, int n, const uint8_t* masks_host, int algo,
+                double rho, int prec, void* cuda_stream, const int* blk, const int64_t* uoff, double gamma1,
+                double gamma2) {
   g_create_error.clear();
   if (!out) return fail(nullptr, BCCB_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
@@ -169,6 +177,9 @@ int bccb_batch_create2(bccb_solver_t* out, const bccb_inst_t* insts, int n, cons
     d.c_off = q.c_off;
     d.g_off = g_off;
     d.lam = q.lam;
+    d.bL1 = blk ? blk[2 * i] : 0;
+    d.bL2 = blk ? blk[2 * i + 1] : 0;
+    d.u_off = uoff ? uoff[i] : q.c_off;
     int cnt = 0;
     const uint8_t* m = masks_host + q.mask_off;
     for (int pos = 0; pos < q.M1 * q.M2; ++pos) mask_idx.push_back(m[pos] ? cnt++ : -1);
@@ -182,16 +193,23 @@ int bccb_batch_create2(bccb_solver_t* out, const bccb_inst_t* insts, int n, cons
     fused[i].c_off = q.c_off;
     fused[i].kappa = 0.f;
     fused[i].kcols = q.L1;
+    fused[i].bl1 = d.bL1;
+    fused[i].bl2 = d.bL2;
     by_shape[{q.L1, q.L2}].push_back(i);
     mm_off += (int64_t)q.M1 * q.M2;
     g_off += (int64_t)q.L1 * q.L2;
     s->total_y = std::max<int64_t>(s->total_y, q.y_off + cnt);
     s->total_c = std::max<int64_t>(s->total_c, q.c_off + (int64_t)q.L1 * q.L2);
+    s->total_u = std::max<int64_t>(s->total_u,
+                                   blk ? d.u_off + (int64_t)d.bL1 * d.bL2 : q.c_off + (int64_t)q.L1 * q.L2);
     s->max_L1 = std::max(s->max_L1, q.L1);
     s->max_L2 = std::max(s->max_L2, q.L2);
   }
   s->total_L = g_off;
   s->total_MM = mm_off;
+  s->toeplitz = blk ? 1 : 0;
+  s->gamma1 = gamma1;
+  s->gamma2 = gamma2;
 
   // class-sorted instance ids; largest grids first so they start earliest
   std::vector<std::pair<int, std::pair<int, int>>> order;
@@ -242,6 +260,13 @@ int bccb_batch_create2(bccb_solver_t* out, const bccb_inst_t* insts, int n, cons
   CREATE_CUDA(dalloc(&s->d_red, n));
   CREATE_CUDA(dalloc(&s->d_tw32, bccb::kTwiddleLen));
   CREATE_CUDA(dalloc(&s->d_tw64, bccb::kTwiddleLen));
+  if (s->toeplitz) {
+    const size_t vb = prec == BCCB_F64 ? sizeof(double2) : sizeof(float2);
+    CREATE_CUDA(cudaMalloc(&s->d_cint, vb * (size_t)s->total_c));
+    CREATE_CUDA(cudaMalloc(&s->d_c0int, vb * (size_t)s->total_c));
+    CREATE_CUDA(dalloc(&s->d_toep_h, s->total_L));
+    CREATE_CUDA(dalloc(&s->d_toep_fb, s->total_L));
+  }
   CREATE_CUDA(cudaMemcpy(s->d_desc, s->h_desc.data(), n * sizeof(InstDesc), cudaMemcpyHostToDevice));
   CREATE_CUDA(cudaMemcpy(s->d_mask_idx, mask_idx.data(), mask_idx.size() * sizeof(int), cudaMemcpyHostToDevice));
   CREATE_CUDA(cudaMemcpy(s->d_fused, fused.data(), n * sizeof(FusedInst), cudaMemcpyHostToDevice));
@@ -276,6 +301,56 @@ int bccb_batch_create2(bccb_solver_t* out, const bccb_inst_t* insts, int n, cons
   return BCCB_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+int bccb_batch_create2(bccb_solver_t* out, const bccb_inst_t* insts, int n, const uint8_t* masks_host, int algo,
+                       double rho, int prec, void* cuda_stream) {
+  return create_impl(out, insts, n, masks_host, algo, rho, prec, cuda_stream, nullptr, nullptr, 0.5, 0.5);
+}
+
+int bccb_batch_create_gamma(bccb_solver_t* out, const bccb_inst_t* insts, int n, const uint8_t* masks_host,
+                            int algo, double rho, int prec, double gamma1, double gamma2, void* cuda_stream) {
+  g_create_error.clear();
+  if (!out) return fail(nullptr, BCCB_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!(gamma1 > 0.0 && gamma1 <= 2.0 && gamma2 > 0.0 && gamma2 <= 2.0))
+    return fail(nullptr, BCCB_ERR_INVALID_ARG, "gamma must lie in (0, 2]");
+  if (gamma1 == 0.5 && gamma2 == 0.5)
+    return bccb_batch_create2(out, insts, n, masks_host, algo, rho, prec, cuda_stream);
+  if (!insts || !masks_host || n < 1) return fail(nullptr, BCCB_ERR_INVALID_ARG, "need n >= 1 instances and masks");
+  if (algo == BCCB_ADMM)
+    return fail(nullptr, BCCB_ERR_UNSUPPORTED,
+                "ADMM with gamma != 1/2: (G + rho I)^-1 of a Toeplitz Gram is not a circulant-embedding product");
+  std::vector<bccb_inst_t> emb(insts, insts + n);
+  std::vector<int> blk(2 * (size_t)n);
+  std::vector<int64_t> uoff(n);
+  int64_t off = 0;
+  for (int i = 0; i < n; ++i) {
+    const bccb_inst_t& q = insts[i];
+    if (!is_pow2(q.L1) || !is_pow2(q.L2) || q.L1 < 16 || q.L2 < 16 || q.L1 > 512 || q.L2 > 512)
+      return fail(nullptr, BCCB_ERR_UNSUPPORTED,
+                  "instance " + std::to_string(i) + ": with gamma != 1/2, L1 and L2 must be powers of two in [16, 512]");
+    if (q.M1 < 1 || q.M2 < 1 || q.M1 > q.L1 || q.M2 > q.L2 || q.M1 > bccb::kToepMaxM || q.M2 > bccb::kToepMaxM)
+      return fail(nullptr, BCCB_ERR_UNSUPPORTED,
+                  "instance " + std::to_string(i) + ": with gamma != 1/2, 1 <= M_i <= L_i and M_i <= 512");
+    int cnt = 0;
+    for (int pos = 0; pos < q.M1 * q.M2; ++pos) cnt += masks_host[q.mask_off + pos] ? 1 : 0;
+    if (cnt > bccb::kToepMaxN)
+      return fail(nullptr, BCCB_ERR_UNSUPPORTED, "instance " + std::to_string(i) + ": more than 1024 elements");
+    blk[2 * i] = q.L1;
+    blk[2 * i + 1] = q.L2;
+    uoff[i] = q.c_off;
+    emb[i].L1 = 2 * q.L1;
+    emb[i].L2 = 2 * q.L2;
+    emb[i].c_off = off;
+    off += (int64_t)emb[i].L1 * emb[i].L2;
+  }
+  return create_impl(out, emb.data(), n, masks_host, algo, rho, prec, cuda_stream, blk.data(), uoff.data(), gamma1,
+                     gamma2);
+}
+
 int bccb_batch_solve(bccb_solver_t s, const void* y_dev, int iters, const void* c0_dev, void* c_out_dev,
                      void* aux_out_dev, int check) {
   if (!s) return fail(nullptr, BCCB_ERR_INVALID_ARG, "solver is NULL");
@@ -287,7 +362,19 @@ int bccb_batch_solve(bccb_solver_t s, const void* y_dev, int iters, const void* 
   if (s->timing) BCCB_CUDA(s, record_timing(s, 0));
   if (s->algo != BCCB_ADMM) BCCB_CUDA(s, bccb::fista_schedule(s, iters));
   const void* y = y_dev;
-  BCCB_CUDA(s, bccb::run_setup(s, y));
+  // a Toeplitz solver iterates on embedded grids: warm start padded in, result cropped out
+  const void* k_c0 = c0_dev;
+  void* k_out = c_out_dev;
+  if (s->toeplitz) {
+    BCCB_CUDA(s, bccb::run_setup_toeplitz(s, y));
+    if (c0_dev) {
+      BCCB_CUDA(s, bccb::toeplitz_pad(s, c0_dev, s->d_c0int));
+      k_c0 = s->d_c0int;
+    }
+    k_out = s->d_cint;
+  } else {
+    BCCB_CUDA(s, bccb::run_setup(s, y));
+  }
   if (s->timing) BCCB_CUDA(s, record_timing(s, 1));
   FusedArgs a{};
   a.insts = s->d_fused;
@@ -295,8 +382,8 @@ int bccb_batch_solve(bccb_solver_t s, const void* y_dev, int iters, const void* 
   a.twiddle = s->d_tw32;
   a.mult = s->d_mult;
   a.bt = s->d_cterm;
-  a.c0 = reinterpret_cast<const float2*>(c0_dev);
-  a.c_out = reinterpret_cast<float2*>(c_out_dev);
+  a.c0 = reinterpret_cast<const float2*>(k_c0);
+  a.c_out = reinterpret_cast<float2*>(k_out);
   a.aux_out = (s->algo == BCCB_ADMM) ? reinterpret_cast<float2*>(aux_out_dev) : nullptr;
   a.iters = iters;
   a.pad_ = 0;
@@ -310,7 +397,7 @@ int bccb_batch_solve(bccb_solver_t s, const void* y_dev, int iters, const void* 
   }
   auto launch_class = [&](const bccb::ShapeClass& c, cudaStream_t st) -> cudaError_t {
     if (c.multipass)
-      return bccb::run_multipass(s, s->d_ids + c.first, c.count, iters, c0_dev, c_out_dev,
+      return bccb::run_multipass(s, s->d_ids + c.first, c.count, iters, k_c0, k_out,
                                  s->algo == BCCB_ADMM ? aux_out_dev : nullptr, st);
     a.ids = s->d_ids + c.first;
     s->launches += 1;
@@ -328,8 +415,14 @@ int bccb_batch_solve(bccb_solver_t s, const void* y_dev, int iters, const void* 
       BCCB_CUDA(s, cudaStreamWaitEvent(s->stream, s->class_done[k], 0));
     }
   }
+  if (s->toeplitz) BCCB_CUDA(s, bccb::toeplitz_crop(s, s->d_cint, c_out_dev));
   if (s->timing) BCCB_CUDA(s, record_timing(s, 2));
-  if (check) BCCB_CUDA(s, bccb::run_check(s, y, c_out_dev));
+  if (check) {
+    if (s->toeplitz)
+      BCCB_CUDA(s, bccb::run_check_toeplitz(s, y, s->d_cint));
+    else
+      BCCB_CUDA(s, bccb::run_check(s, y, c_out_dev));
+  }
   if (s->timing) BCCB_CUDA(s, record_timing(s, 3));
   s->last_checked = check != 0;
   return BCCB_OK;
@@ -341,11 +434,11 @@ int bccb_batch_solve_host(bccb_solver_t s, const void* y_host, int iters, void* 
   BCCB_CUDA(s, cudaSetDevice(s->device));
   const size_t vb = s->prec == BCCB_F64 ? sizeof(double2) : sizeof(float2);
   if (!s->d_y_stage) BCCB_CUDA(s, dalloc(&s->d_y_stage, s->total_y * vb / sizeof(float2)));
-  if (!s->d_c_stage) BCCB_CUDA(s, dalloc(&s->d_c_stage, s->total_c * vb / sizeof(float2)));
+  if (!s->d_c_stage) BCCB_CUDA(s, dalloc(&s->d_c_stage, s->total_u * vb / sizeof(float2)));
   BCCB_CUDA(s, cudaMemcpyAsync(s->d_y_stage, y_host, s->total_y * vb, cudaMemcpyHostToDevice, s->stream));
   int st = bccb_batch_solve(s, s->d_y_stage, iters, nullptr, s->d_c_stage, nullptr, check);
   if (st != BCCB_OK) return st;
-  BCCB_CUDA(s, cudaMemcpyAsync(c_out_host, s->d_c_stage, s->total_c * vb, cudaMemcpyDeviceToHost, s->stream));
+  BCCB_CUDA(s, cudaMemcpyAsync(c_out_host, s->d_c_stage, s->total_u * vb, cudaMemcpyDeviceToHost, s->stream));
   BCCB_CUDA(s, cudaStreamSynchronize(s->stream));
   return BCCB_OK;
 }
@@ -370,6 +463,7 @@ int bccb_batch_results(bccb_solver_t s, double* kkt, double* obj, double* lam, d
 int bccb_batch_get(bccb_solver_t s, int what, void* dst_dev) {
   if (!s) return fail(nullptr, BCCB_ERR_INVALID_ARG, "solver is NULL");
   if (!dst_dev || what < 0 || what > 3) return fail(s, BCCB_ERR_INVALID_ARG, "bad what / dst");
+  if (s->toeplitz) return fail(s, BCCB_ERR_UNSUPPORTED, "the grids of a gamma != 1/2 solver are embedded 2L1 x 2L2");
   BCCB_CUDA(s, cudaSetDevice(s->device));
   const void* src = what == 0 ? (const void*)s->d_lam64
                   : what == 1 ? (const void*)s->d_b64
@@ -572,6 +666,7 @@ int bccb_unrolled_fwd(bccb_solver_t s, const void* y_dev, int layers, const floa
   if (!s) return fail(nullptr, BCCB_ERR_INVALID_ARG, "solver is NULL");
   s->last_error.clear();
   if (s->algo != BCCB_FISTA) return fail(s, BCCB_ERR_INVALID_ARG, "the unrolled network needs a FISTA solver");
+  if (s->toeplitz) return fail(s, BCCB_ERR_UNSUPPORTED, "the unrolled network needs gamma = 1/2");
   for (const auto& c : s->classes)
     if (c.multipass) return fail(s, BCCB_ERR_UNSUPPORTED, "the unrolled network needs FP32 grids up to 256");
   if (!y_dev || !c_out_dev || !scale_dev || !thresh_dev || layers < 1)
@@ -611,6 +706,7 @@ int bccb_unrolled_bwd(bccb_solver_t s, int layers, const float* scale_dev, const
   if (!s) return fail(nullptr, BCCB_ERR_INVALID_ARG, "solver is NULL");
   s->last_error.clear();
   if (s->algo != BCCB_FISTA) return fail(s, BCCB_ERR_INVALID_ARG, "the unrolled network needs a FISTA solver");
+  if (s->toeplitz) return fail(s, BCCB_ERR_UNSUPPORTED, "the unrolled network needs gamma = 1/2");
   if (!scale_dev || !thresh_dev || !saved_dev || !grad_c_dev || !grad_scale_dev || !grad_thresh_dev || layers < 1)
     return fail(s, BCCB_ERR_INVALID_ARG, "bad pointer or layers");
   if (s->beta_len < layers) return fail(s, BCCB_ERR_INVALID_ARG, "run bccb_unrolled_fwd with these layers first");
@@ -650,6 +746,7 @@ int bccb_batch_set_method(bccb_solver_t s, int method) {
     return BCCB_OK;
   }
   if (s->prec != BCCB_F32) return fail(s, BCCB_ERR_UNSUPPORTED, "the dense method runs in complex64 only");
+  if (s->toeplitz) return fail(s, BCCB_ERR_UNSUPPORTED, "the dense method builds the BCCB Gram (gamma = 1/2) only");
   size_t bytes = 0;
   for (const InstDesc& d : s->h_desc) {
     if (s->algo == BCCB_ADMM && (d.M1 > d.L1 || d.M2 > d.L2))

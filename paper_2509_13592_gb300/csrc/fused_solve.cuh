@@ -48,6 +48,8 @@ struct FusedInst {
   int64_t c_off;  // offset of this instance's solution in c_out / aux_out / c0
   float kappa;    // threshold mu*lam (ISTA/FISTA) or lam/rho (ADMM), set by the setup kernels
   int kcols;      // 1 + the largest Fourier column p1 where q or Bt is nonzero (set by setup)
+  int bl1 = 0;    // > 0: only the block l1 < bl1, l2 < bl2 of the grid is the unknown (the
+  int bl2 = 0;    //   circulant embedding of a Toeplitz Gram); the update keeps 0 outside it
 };
 
 struct FusedArgs {
@@ -754,9 +756,15 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
 
   // The pointwise update of one element after the inverse transform: returns the
   // next iteration's FFT input (z for ISTA/FISTA, z - v for ADMM).
+  const bool blocked = in.bl1 != 0;
   auto update = [&](int row, int e, float2 g, float beta, bool last, float sc, float kap, float2* save_t) -> float2 {
     const int sidx = row * L1 + e;
     if constexpr (!ADMM) {
+      if (blocked && (e >= in.bl1 || crank + C * row >= in.bl2)) {
+        cta.s0[sidx] = make_float2(0.f, 0.f);
+        cta.s1[sidx] = make_float2(0.f, 0.f);
+        return make_float2(0.f, 0.f);
+      }
       const float2 c_old = cta.s0[sidx];
       const float2 x = cta.s1[sidx];  // z^(t)
       float2 un;

@@ -95,10 +95,16 @@ __global__ void mp_rows_kernel(MpArgs<V> a) {
     const T kappa = (T)(a.algo == 2 ? p.lam / a.rho : p.mu * p.lam);
     const T beta = (a.algo == 1) ? a.beta[a.it] : (T)0;
     V* aux = a.aux ? a.aux + d.c_off + (int64_t)row * L1 : nullptr;
+    const bool outside_rows = d.bL1 != 0 && row >= d.bL2;
     for (int e = threadIdx.x; e < L1; e += blockDim.x) {
       const V g = res[e];
       V next;
-      if (a.algo != 2) {
+      if (d.bL1 != 0 && (outside_rows || e >= d.bL1)) {
+        // outside the unknown block of a circulant embedding: stays 0
+        s0[e] = cmk<V>((T)0, (T)0);
+        s1[e] = cmk<V>((T)0, (T)0);
+        next = cmk<V>((T)0, (T)0);
+      } else if (a.algo != 2) {
         const V c_old = s0[e];
         const V xin = (a.algo == 1) ? s1[e] : c_old;
         const V cn = shrink(csub(xin, g), kappa);

@@ -1,8 +1,9 @@
 // Peak extraction on |c| and the harmonic-to-angle map (Section II-A).
 //
 // The support of the recovered c marks harmonic pairs (f1, f2) on the uniform grids
-// f_{i,l} = -1/2 + l/L_i (eq:uniform_grid with gamma_i = 1/2), and each pair gives the
-// angles through f1 = gamma1 cos(phi) sin(theta), f2 = gamma2 sin(phi) sin(theta).
+// f_{i,l} = -gamma_i + l 2 gamma_i / L_i (eq:uniform_grid; gamma_i = 1/2 for half-wavelength
+// spacing), and each pair gives the angles through f1 = gamma1 cos(phi) sin(theta),
+// f2 = gamma2 sin(phi) sin(theta).
 // The paper states the map but no peak-picking rule; the one used:
 //   m(p) = |c(p)|^2 in c's precision (products and sum rounded separately);
 //   p is a peak when m(p) > 0, m(p) >= rel^2 max m and, for each of its 8 cyclic
@@ -84,8 +85,9 @@ __device__ void block_scan(unsigned f, unsigned& excl, unsigned& total, unsigned
 
 template <typename V>
 __global__ void __launch_bounds__(kPeakThreads) peaks_kernel(const InstDesc* __restrict__ desc, const V* __restrict__ c,
-                                                             int K, double rel2, int* idx_out, double* mag_out,
-                                                             double* harm_out, double* ang_out, int* count_out) {
+                                                             int K, double rel2, double g1, double g2, int* idx_out,
+                                                             double* mag_out, double* harm_out, double* ang_out,
+                                                             int* count_out) {
   using P = PeakT<V>;
   using M = typename P::M;
   using Key = typename P::Key;
@@ -98,8 +100,9 @@ __global__ void __launch_bounds__(kPeakThreads) peaks_kernel(const InstDesc* __r
   __shared__ unsigned s_need, s_ngt;
 
   const InstDesc d = desc[blockIdx.x];
-  const int L1 = d.L1, L2 = d.L2, L = L1 * L2;
-  const V* ci = c + d.c_off;
+  // the caller's grid (the block of a circulant embedding when bL1 > 0)
+  const int L1 = d.bL1 ? d.bL1 : d.L1, L2 = d.bL1 ? d.bL2 : d.L2, L = L1 * L2;
+  const V* ci = c + d.u_off;
   const int tid = threadIdx.x, nt = blockDim.x;
 
   // ---- max m and the threshold
@@ -248,12 +251,14 @@ __global__ void __launch_bounds__(kPeakThreads) peaks_kernel(const InstDesc* __r
     if (i < nsel) {
       const int p = sidx[i];
       const int l1 = p % L1, l2 = p / L1;
-      const double f1 = -0.5 + (double)l1 / (double)L1, f2 = -0.5 + (double)l2 / (double)L2;
+      // product and sum rounded separately (no contraction), as the grid is defined
+      const double f1 = __dadd_rn(-g1, __dmul_rn((double)l1, 2.0 * g1 / (double)L1));
+      const double f2 = __dadd_rn(-g2, __dmul_rn((double)l2, 2.0 * g2 / (double)L2));
       idx_out[o] = p;
       mag_out[o] = P::root(P::value(skey[i]));
       harm_out[2 * o] = f1;
       harm_out[2 * o + 1] = f2;
-      const double u1 = 2.0 * f1, u2 = 2.0 * f2;
+      const double u1 = f1 / g1, u2 = f2 / g2;
       const double s = __dadd_rn(__dmul_rn(u1, u1), __dmul_rn(u2, u2));
       if (s <= 1.0) {
         ang_out[2 * o] = atan2(u2, u1);
@@ -281,10 +286,12 @@ cudaError_t run_peaks(bccb_solver* s, const void* c_dev, int K, double rel_thres
   const double rel2 = rel_thresh * rel_thresh;
   if (s->prec == 1)
     peaks_kernel<double2><<<s->n, kPeakThreads, 0, s->stream>>>(
-        s->d_desc, reinterpret_cast<const double2*>(c_dev), K, rel2, idx, mag, harm, ang, count);
+        s->d_desc, reinterpret_cast<const double2*>(c_dev), K, rel2, s->gamma1, s->gamma2, idx, mag, harm, ang,
+        count);
   else
     peaks_kernel<float2><<<s->n, kPeakThreads, 0, s->stream>>>(
-        s->d_desc, reinterpret_cast<const float2*>(c_dev), K, rel2, idx, mag, harm, ang, count);
+        s->d_desc, reinterpret_cast<const float2*>(c_dev), K, rel2, s->gamma1, s->gamma2, idx, mag, harm, ang,
+        count);
   s->launches += 1;
   return cudaGetLastError();
 }

@@ -17,6 +17,7 @@
 // memory with each row / column tile staged in shared memory.
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "fft_smem.cuh"
@@ -307,6 +308,304 @@ cudaError_t fft2_64(bccb_solver* s, double2* grid, int inv) {
   return cudaGetLastError();
 }
 
+
+// ------------------------------------------------------------------------------------------
+// Element spacing gamma != 1/2 (Section III-A): on the grids f_{i,l} = -gamma_i + l 2 gamma_i/L_i
+// (eq:uniform_grid) the Gram G = A^H A is block Toeplitz with Toeplitz blocks,
+//   G[l, l'] = g(l1 - l1', l2 - l2'),  g(d1, d2) = sum_n exp(+j 2 pi (2 gamma1 d1 m1_n / L1 + 2 gamma2 d2 m2_n / L2)),
+// for lags |d_i| < L_i.  Its product is the top-left L1 x L2 block of the product with the
+// 2L1 x 2L2 circulant whose first column holds g at lags d (d >= 0) and d - 2L (d > L), and 0 at
+// d = L (the lag no pair of block entries uses): the same FFT2 iteration then runs on the
+// embedded grid with the unknown kept at 0 outside the block.  Here the descriptor's L1 x L2 is
+// the embedded grid and bL1 x bL2 the block (the caller's grid).  mu = 1/lambda_max(G) =
+// 1/lambda_max(A A^H) (eq:ista) comes from an FP32 power iteration on the N x N matrix A A^H,
+// finished by its FP64 Rayleigh quotient (accurate to the square of the vector's error).
+// ------------------------------------------------------------------------------------------
+
+// lag of embedded index e on an axis of block length Lb (embedded 2 Lb); Lb itself is unused
+__device__ __forceinline__ int toep_lag(int e, int Lb) { return e < Lb ? e : e - 2 * Lb; }
+
+// h[e1][m2] = sum over kept m1 of exp(+j 2 pi 2 gamma1 d1 m1 / bL1), d1 = lag(e1); 0 at e1 = bL1
+__global__ void toep_col1_kernel(const InstDesc* __restrict__ desc, const int* __restrict__ mask_idx, double g1,
+                                 double2* h) {
+  const InstDesc d = desc[blockIdx.x];
+  const int* mi = mask_idx + d.mask_off;
+  for (int t = blockIdx.y * blockDim.x + threadIdx.x; t < d.L1 * d.M2; t += gridDim.y * blockDim.x) {
+    const int e1 = t % d.L1, m2 = t / d.L1;
+    double2 acc = make_double2(0.0, 0.0);
+    if (e1 != d.bL1) {
+      const double w = 2.0 * g1 * (double)toep_lag(e1, d.bL1) / (double)d.bL1;
+      for (int m1 = 0; m1 < d.M1; ++m1) {
+        if (mi[m1 + m2 * d.M1] < 0) continue;
+        double sn, cs;
+        sincospi(2.0 * w * (double)m1, &sn, &cs);
+        acc.x += cs;
+        acc.y += sn;
+      }
+    }
+    h[d.g_off + t] = acc;
+  }
+}
+
+// first column of the embedding: sum_m2 h[e1][m2] exp(+j 2 pi 2 gamma2 d2 m2 / bL2); 0 at e2 = bL2
+__global__ void toep_col2_kernel(const InstDesc* __restrict__ desc, const double2* __restrict__ h, double g2,
+                                 double2* w) {
+  const InstDesc d = desc[blockIdx.x];
+  const int L = d.L1 * d.L2;
+  for (int cell = blockIdx.y * blockDim.x + threadIdx.x; cell < L; cell += gridDim.y * blockDim.x) {
+    const int e1 = cell % d.L1, e2 = cell / d.L1;
+    double2 acc = make_double2(0.0, 0.0);
+    if (e2 != d.bL2) {
+      const double wt = 2.0 * g2 * (double)toep_lag(e2, d.bL2) / (double)d.bL2;
+      for (int m2 = 0; m2 < d.M2; ++m2) {
+        const double2 hv = h[d.g_off + e1 + (int64_t)m2 * d.L1];
+        double sn, cs;
+        sincospi(2.0 * wt * (double)m2, &sn, &cs);
+        acc.x += hv.x * cs - hv.y * sn;
+        acc.y += hv.x * sn + hv.y * cs;
+      }
+    }
+    w[d.g_off + cell] = acc;
+  }
+}
+
+// b = A^H y on the block, 0 elsewhere: hb[l1][m2] = sum_m1 exp(+j 2 pi f1 m1) y(m1, m2), then
+// b[l2][l1] = sum_m2 exp(+j 2 pi f2 m2) hb[l1][m2], with f_i = -gamma_i + l 2 gamma_i / bL_i
+template <typename Y>
+__global__ void toep_b1_kernel(const InstDesc* __restrict__ desc, const int* __restrict__ mask_idx,
+                               const Y* __restrict__ y, double g1, double2* h) {
+  const InstDesc d = desc[blockIdx.x];
+  const int* mi = mask_idx + d.mask_off;
+  const Y* yi = y + d.y_off;
+  for (int t = blockIdx.y * blockDim.x + threadIdx.x; t < d.bL1 * d.M2; t += gridDim.y * blockDim.x) {
+    const int l1 = t % d.bL1, m2 = t / d.bL1;
+    const double f1 = -g1 + (double)l1 * (2.0 * g1 / (double)d.bL1);
+    double2 acc = make_double2(0.0, 0.0);
+    for (int m1 = 0; m1 < d.M1; ++m1) {
+      const int n = mi[m1 + m2 * d.M1];
+      if (n < 0) continue;
+      double sn, cs;
+      sincospi(2.0 * f1 * (double)m1, &sn, &cs);
+      const double yx = (double)yi[n].x, yy = (double)yi[n].y;
+      acc.x += cs * yx - sn * yy;
+      acc.y += cs * yy + sn * yx;
+    }
+    h[d.g_off + t] = acc;
+  }
+}
+
+__global__ void toep_b2_kernel(const InstDesc* __restrict__ desc, const double2* __restrict__ h, double g2,
+                               double2* b) {
+  const InstDesc d = desc[blockIdx.x];
+  const int L = d.L1 * d.L2;
+  for (int cell = blockIdx.y * blockDim.x + threadIdx.x; cell < L; cell += gridDim.y * blockDim.x) {
+    const int e1 = cell % d.L1, e2 = cell / d.L1;
+    double2 acc = make_double2(0.0, 0.0);
+    if (e1 < d.bL1 && e2 < d.bL2) {
+      const double f2 = -g2 + (double)e2 * (2.0 * g2 / (double)d.bL2);
+      for (int m2 = 0; m2 < d.M2; ++m2) {
+        const double2 hv = h[d.g_off + e1 + (int64_t)m2 * d.bL1];
+        double sn, cs;
+        sincospi(2.0 * f2 * (double)m2, &sn, &cs);
+        acc.x += hv.x * cs - hv.y * sn;
+        acc.y += hv.x * sn + hv.y * cs;
+      }
+    }
+    b[d.g_off + cell] = acc;
+  }
+}
+
+// lambda_max(A A^H): (A A^H)[n, n'] = S1(m1_n - m1_n') S2(m2_n - m2_n') with
+// S_i(k) = sum_{l < bL_i} exp(-j 2 pi f_{i,l} k).  One CTA per instance; N <= kToepMaxN.
+
+__device__ double2 toep_s(int k, int Lb, double g) {
+  double2 acc = make_double2(0.0, 0.0);
+  for (int l = 0; l < Lb; ++l) {
+    const double f = -g + (double)l * (2.0 * g / (double)Lb);
+    double sn, cs;
+    sincospi(-2.0 * f * (double)k, &sn, &cs);
+    acc.x += cs;
+    acc.y += sn;
+  }
+  return acc;
+}
+
+__global__ void __launch_bounds__(1024) toep_mu_kernel(const InstDesc* __restrict__ desc,
+                                                       const int* __restrict__ mask_idx, double g1, double g2,
+                                                       InstParams* par) {
+  extern __shared__ double2 tsm[];
+  const InstDesc d = desc[blockIdx.x];
+  const int N = d.N, M1 = d.M1, M2 = d.M2;
+  double2* s1 = tsm;                        // 2 M1 - 1, index k + M1 - 1
+  double2* s2 = s1 + (2 * M1 - 1);          // 2 M2 - 1
+  float2* f1 = reinterpret_cast<float2*>(s2 + (2 * M2 - 1));
+  float2* f2 = f1 + (2 * M1 - 1);
+  float2* v = f2 + (2 * M2 - 1);            // N
+  float2* w = v + N;                        // N
+  int* pm1 = reinterpret_cast<int*>(w + N);  // N
+  int* pm2 = pm1 + N;                        // N
+  __shared__ double red[32];
+  const int* mi = mask_idx + d.mask_off;
+  for (int k = threadIdx.x; k < 2 * M1 - 1; k += blockDim.x) {
+    s1[k] = toep_s(k - (M1 - 1), d.bL1, g1);
+    f1[k] = make_float2((float)s1[k].x, (float)s1[k].y);
+  }
+  for (int k = threadIdx.x; k < 2 * M2 - 1; k += blockDim.x) {
+    s2[k] = toep_s(k - (M2 - 1), d.bL2, g2);
+    f2[k] = make_float2((float)s2[k].x, (float)s2[k].y);
+  }
+  for (int cell = threadIdx.x; cell < M1 * M2; cell += blockDim.x) {
+    const int n = mi[cell];
+    if (n >= 0) {
+      pm1[n] = cell % M1;
+      pm2[n] = cell / M1;
+    }
+  }
+  for (int n = threadIdx.x; n < N; n += blockDim.x) v[n] = make_float2(1.0f + 0.25f * __sinf(0.7f * n), 0.0f);
+  __syncthreads();
+  double rq_prev = -1.0, rq = 0.0;
+  for (int outer = 0; outer < 256; ++outer) {
+    for (int it = 0; it < 64; ++it) {
+      // w = B v (FP32), then v = w / ||w||
+      float nrm = 0.f;
+      for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        const int a1 = pm1[n] + M1 - 1, a2 = pm2[n] + M2 - 1;
+        float ax = 0.f, ay = 0.f;
+        for (int q = 0; q < N; ++q) {
+          const float2 p = f1[a1 - pm1[q]], r = f2[a2 - pm2[q]];
+          const float bx = p.x * r.x - p.y * r.y, by = p.x * r.y + p.y * r.x;
+          const float2 vq = v[q];
+          ax += bx * vq.x - by * vq.y;
+          ay += bx * vq.y + by * vq.x;
+        }
+        w[n] = make_float2(ax, ay);
+        nrm += ax * ax + ay * ay;
+      }
+      const double tot = block_reduce((double)nrm, SumOp(), red, 0.0);
+      const float inv = (float)(1.0 / sqrt(tot > 0.0 ? tot : 1.0));
+      for (int n = threadIdx.x; n < N; n += blockDim.x) v[n] = make_float2(w[n].x * inv, w[n].y * inv);
+      __syncthreads();
+    }
+    // FP64 Rayleigh quotient v^H B v / v^H v
+    double num = 0.0, den = 0.0;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+      const int a1 = pm1[n] + M1 - 1, a2 = pm2[n] + M2 - 1;
+      double ax = 0.0, ay = 0.0;
+      for (int q = 0; q < N; ++q) {
+        const double2 p = s1[a1 - pm1[q]], r = s2[a2 - pm2[q]];
+        const double bx = p.x * r.x - p.y * r.y, by = p.x * r.y + p.y * r.x;
+        const double vx = v[q].x, vy = v[q].y;
+        ax += bx * vx - by * vy;
+        ay += bx * vy + by * vx;
+      }
+      const double vx = v[n].x, vy = v[n].y;
+      num += vx * ax + vy * ay;  // Re(conj(v_n) (B v)_n)
+      den += vx * vx + vy * vy;
+    }
+    num = block_reduce(num, SumOp(), red, 0.0);
+    den = block_reduce(den, SumOp(), red, 0.0);
+    rq = num / den;
+    if (fabs(rq - rq_prev) <= 1e-14 * rq) break;
+    rq_prev = rq;
+  }
+  if (threadIdx.x == 0) {
+    par[blockIdx.x].mu = 1.0 / rq;
+    par[blockIdx.x].lam_top = rq;
+  }
+}
+
+// Lambda_ext (real part of the embedding's spectrum), q = mu Lambda_ext / L and
+// Bt = mu FFT2(b)/L over the embedded grid (L = its size); the whole spectrum is active
+__global__ void toep_mult_kernel(const InstDesc* __restrict__ desc, const double2* __restrict__ lam_c,
+                                 const double2* __restrict__ fb, const InstParams* __restrict__ par,
+                                 double* lam64, float* mult, float2* bt, double* mult64, double2* bt64,
+                                 FusedInst* fused) {
+  const InstDesc d = desc[blockIdx.x];
+  const int L = d.L1 * d.L2;
+  const double mu = par[blockIdx.x].mu, inv_L = 1.0 / (double)L;
+  for (int cell = blockIdx.y * blockDim.x + threadIdx.x; cell < L; cell += gridDim.y * blockDim.x) {
+    const double lv = lam_c[d.g_off + cell].x;
+    const double2 f = fb[d.g_off + cell];
+    const double m = mu * lv * inv_L;
+    lam64[d.g_off + cell] = lv;
+    mult[d.g_off + cell] = (float)m;
+    bt[d.g_off + cell] = make_float2((float)(mu * f.x * inv_L), (float)(mu * f.y * inv_L));
+    if (mult64) {
+      mult64[d.g_off + cell] = m;
+      bt64[d.g_off + cell] = make_double2(mu * f.x * inv_L, mu * f.y * inv_L);
+    }
+  }
+  if (threadIdx.x == 0 && blockIdx.y == 0) fused[blockIdx.x].kcols = d.L1;
+}
+
+// KKT residual and objective on the block: r = b - G c with G c the block of the
+// (unnormalised) embedded product in gc; objective 1/2 ||y||^2 - Re(b^H c) + 1/2 Re(c^H G c) + lam ||c||_1
+template <typename C>
+__global__ void toep_kkt_kernel(const InstDesc* __restrict__ desc, const double2* __restrict__ b64,
+                                const double2* __restrict__ gc, const C* __restrict__ c, const C* __restrict__ y,
+                                const InstParams* __restrict__ par, double* kkt, double* obj) {
+  __shared__ double sh[32];
+  const InstDesc d = desc[blockIdx.x];
+  const double lam = par[blockIdx.x].lam;
+  const double inv_L = 1.0 / (double)(d.L1 * d.L2);
+  double worst = 0.0, l1 = 0.0, bc = 0.0, cgc = 0.0, yy = 0.0;
+  for (int t = threadIdx.x; t < d.bL1 * d.bL2; t += blockDim.x) {
+    const int cell = (t % d.bL1) + (t / d.bL1) * d.L1;
+    const double2 bv = b64[d.g_off + cell];
+    const double2 g = make_double2(gc[d.g_off + cell].x * inv_L, gc[d.g_off + cell].y * inv_L);
+    const double rx = bv.x - g.x, ry = bv.y - g.y;
+    const C cv = c[d.c_off + cell];
+    const double cx = cv.x, cy = cv.y;
+    const double mag = sqrt(cx * cx + cy * cy);
+    double viol;
+    if (mag > 0.0) {
+      const double ex = rx - lam * cx / mag, ey = ry - lam * cy / mag;
+      viol = sqrt(ex * ex + ey * ey);
+    } else {
+      viol = fmax(sqrt(rx * rx + ry * ry) - lam, 0.0);
+    }
+    worst = fmax(worst, viol);
+    l1 += mag;
+    bc += bv.x * cx + bv.y * cy;  // Re(conj(b) c)
+    cgc += cx * g.x + cy * g.y;   // Re(conj(c) G c)
+  }
+  for (int n = threadIdx.x; n < d.N; n += blockDim.x) {
+    const C v = y[d.y_off + n];
+    yy += (double)v.x * v.x + (double)v.y * v.y;
+  }
+  worst = block_reduce(worst, MaxOp(), sh, 0.0);
+  l1 = block_reduce(l1, SumOp(), sh, 0.0);
+  bc = block_reduce(bc, SumOp(), sh, 0.0);
+  cgc = block_reduce(cgc, SumOp(), sh, 0.0);
+  yy = block_reduce(yy, SumOp(), sh, 0.0);
+  if (threadIdx.x == 0) {
+    kkt[blockIdx.x] = lam > 0.0 ? worst / lam : worst;
+    obj[blockIdx.x] = 0.5 * yy - bc + 0.5 * cgc + lam * l1;
+  }
+}
+
+// caller's packing (block grids at u_off) <-> embedded grids (at c_off, zero outside the block)
+template <typename C>
+__global__ void toep_pad_kernel(const InstDesc* __restrict__ desc, const C* __restrict__ cu, C* ci) {
+  const InstDesc d = desc[blockIdx.x];
+  const int L = d.L1 * d.L2;
+  for (int cell = blockIdx.y * blockDim.x + threadIdx.x; cell < L; cell += gridDim.y * blockDim.x) {
+    const int e1 = cell % d.L1, e2 = cell / d.L1;
+    C v;
+    v.x = 0;
+    v.y = 0;
+    if (cu && e1 < d.bL1 && e2 < d.bL2) v = cu[d.u_off + e1 + (int64_t)e2 * d.bL1];
+    ci[d.c_off + cell] = v;
+  }
+}
+
+template <typename C>
+__global__ void toep_crop_kernel(const InstDesc* __restrict__ desc, const C* __restrict__ ci, C* cu) {
+  const InstDesc d = desc[blockIdx.x];
+  for (int t = blockIdx.y * blockDim.x + threadIdx.x; t < d.bL1 * d.bL2; t += gridDim.y * blockDim.x)
+    cu[d.u_off + t] = ci[d.c_off + (t % d.bL1) + (int64_t)(t / d.bL1) * d.L1];
+}
+
 }  // namespace
 
 cudaError_t fill_twiddles(bccb_solver* s) {
@@ -396,6 +695,92 @@ cudaError_t run_check(bccb_solver* s, const void* y_dev, const void* c_dev) {
 cudaError_t prepare_fp64_passes(int max_L2) {
   const int col_smem = 2 * max_L2 * cols_per_block(max_L2) * (int)sizeof(double2);
   return cudaFuncSetAttribute(fft64_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem);
+}
+
+
+size_t toeplitz_mu_smem(int N, int M1, int M2) {
+  return (size_t)(2 * M1 - 1 + 2 * M2 - 1) * sizeof(double2) + (size_t)(2 * M1 - 1 + 2 * M2 - 1) * sizeof(float2) +
+         (size_t)2 * N * sizeof(float2) + (size_t)2 * N * sizeof(int);
+}
+
+cudaError_t run_setup_toeplitz(bccb_solver* s, const void* y_dev) {
+  const dim3 gc = grid_cells(s);
+  cudaError_t err;
+  toep_col1_kernel<<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_mask_idx, s->gamma1, s->d_toep_h);
+  toep_col2_kernel<<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_toep_h, s->gamma2, s->d_w64);
+  if ((err = fft2_64(s, s->d_w64, 0)) != cudaSuccess) return err;  // spectrum of the embedding
+  if (s->prec == 1)
+    toep_b1_kernel<double2><<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_mask_idx,
+                                                            static_cast<const double2*>(y_dev), s->gamma1, s->d_toep_h);
+  else
+    toep_b1_kernel<float2><<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_mask_idx,
+                                                           static_cast<const float2*>(y_dev), s->gamma1, s->d_toep_h);
+  toep_b2_kernel<<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_toep_h, s->gamma2, s->d_b64);
+  int maxN = 0, maxM1 = 0, maxM2 = 0;
+  for (const InstDesc& d : s->h_desc) {
+    maxN = std::max(maxN, d.N);
+    maxM1 = std::max(maxM1, d.M1);
+    maxM2 = std::max(maxM2, d.M2);
+  }
+  const size_t mu_smem = toeplitz_mu_smem(maxN, maxM1, maxM2);
+  if ((err = cudaFuncSetAttribute(toep_mu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mu_smem)) !=
+      cudaSuccess)
+    return err;
+  toep_mu_kernel<<<s->n, 1024, mu_smem, s->stream>>>(s->d_desc, s->d_mask_idx,
+                                                                                  s->gamma1, s->gamma2, s->d_par);
+  lam_kappa_kernel<<<s->n, kThreads, 0, s->stream>>>(s->d_desc, s->d_b64, s->d_par, s->d_fused, s->algo, s->rho);
+  if ((err = cudaMemcpyAsync(s->d_toep_fb, s->d_b64, sizeof(double2) * (size_t)s->total_L, cudaMemcpyDeviceToDevice,
+                             s->stream)) != cudaSuccess)
+    return err;
+  if ((err = fft2_64(s, s->d_toep_fb, 0)) != cudaSuccess) return err;
+  toep_mult_kernel<<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_w64, s->d_toep_fb, s->d_par, s->d_lam64, s->d_mult,
+                                                   s->d_cterm, s->d_mult64, s->d_bt64, s->d_fused);
+  s->launches += 8;
+  return cudaGetLastError();
+}
+
+template <typename V>
+cudaError_t run_check_toeplitz_t(bccb_solver* s, const V* y_dev, const V* c_int) {
+  const dim3 gc = grid_cells(s);
+  load_solution_kernel<V><<<gc, kThreads, 0, s->stream>>>(s->d_desc, c_int, s->d_w64);
+  cudaError_t err;
+  if ((err = fft2_64(s, s->d_w64, 0)) != cudaSuccess) return err;
+  mul_lambda_kernel<<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_lam64, s->d_w64);
+  if ((err = fft2_64(s, s->d_w64, 1)) != cudaSuccess) return err;
+  toep_kkt_kernel<V><<<s->n, kThreads, 0, s->stream>>>(s->d_desc, s->d_b64, s->d_w64, c_int, y_dev, s->d_par,
+                                                        s->d_kkt, s->d_obj);
+  s->launches += 3;
+  return cudaGetLastError();
+}
+
+cudaError_t run_check_toeplitz(bccb_solver* s, const void* y_dev, const void* c_int) {
+  if (s->prec == 1)
+    return run_check_toeplitz_t<double2>(s, static_cast<const double2*>(y_dev), static_cast<const double2*>(c_int));
+  return run_check_toeplitz_t<float2>(s, static_cast<const float2*>(y_dev), static_cast<const float2*>(c_int));
+}
+
+cudaError_t toeplitz_pad(bccb_solver* s, const void* c_user, void* c_int) {
+  const dim3 gc = grid_cells(s);
+  if (s->prec == 1)
+    toep_pad_kernel<double2><<<gc, kThreads, 0, s->stream>>>(s->d_desc, static_cast<const double2*>(c_user),
+                                                             static_cast<double2*>(c_int));
+  else
+    toep_pad_kernel<float2><<<gc, kThreads, 0, s->stream>>>(s->d_desc, static_cast<const float2*>(c_user),
+                                                            static_cast<float2*>(c_int));
+  s->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t toeplitz_crop(bccb_solver* s, const void* c_int, void* c_user) {
+  const dim3 gc = grid_cells(s);
+  if (s->prec == 1)
+    toep_crop_kernel<double2><<<gc, kThreads, 0, s->stream>>>(s->d_desc, static_cast<const double2*>(c_int),
+                                                              static_cast<double2*>(c_user));
+  else
+    toep_crop_kernel<float2><<<gc, kThreads, 0, s->stream>>>(s->d_desc, static_cast<const float2*>(c_int),
+                                                             static_cast<float2*>(c_user));
+  s->launches += 1;
+  return cudaGetLastError();
 }
 
 }  // namespace bccb

@@ -20,6 +20,10 @@ struct InstDesc {
   int64_t c_off;     // complex elements into the solution buffer
   int64_t g_off;     // elements into the per-grid arenas (L1*L2 each)
   double lam;        // absolute lam, or fraction (see lam_is_frac)
+  // element spacing gamma != 1/2 (Toeplitz Gram): L1 x L2 above is the 2 bL1 x 2 bL2
+  // circulant embedding and bL1 x bL2 the caller's grid; 0 for the BCCB case
+  int bL1 = 0, bL2 = 0;
+  int64_t u_off = 0;  // the caller's offset of this instance's solution (= c_off for BCCB)
 };
 
 // Per-instance scalars produced on the device by the setup kernels.
@@ -97,6 +101,15 @@ struct bccb_solver {
   void* d_mp_work = nullptr;
   void* d_mp_s0 = nullptr;
   void* d_mp_s1 = nullptr;
+  // element spacings (Section II-A); toeplitz = 1 when either differs from 1/2: the
+  // kernels then run on the 2 L1 x 2 L2 circulant embedding (toeplitz.cu)
+  int toeplitz = 0;
+  double gamma1 = 0.5, gamma2 = 0.5;
+  int64_t total_u = 0;            // length of the caller's packed solution
+  void* d_cint = nullptr;         // embedded solution grids (Toeplitz)
+  void* d_c0int = nullptr;        // embedded warm start (Toeplitz)
+  double2* d_toep_h = nullptr;    // FP64 scratch of the Toeplitz setup
+  double2* d_toep_fb = nullptr;   // FP64 FFT2 of the zero-padded b (Toeplitz)
   // iteration engine: 0 = FFT (fused / multi-pass), 1 = dense L x L Gram (dense.cu)
   int method = 0;
   float2* d_gram = nullptr;       // per instance L x L complex64, row-major
@@ -129,6 +142,15 @@ const FusedEntry* learned_lookup(int L1, int L2);
 // dense.cu: build the stored Gram matrices (synchronises) and run the dense iterations
 cudaError_t dense_prepare(bccb_solver* s);
 cudaError_t run_dense(bccb_solver* s, int iters, const void* c0, void* c_out, void* aux);
+// toeplitz.cu: setup and check on the circulant embedding, and the pad / crop between the
+// caller's packing and the embedded grids
+constexpr int kToepMaxN = 1024;  // elements per instance (the N x N power iteration runs in one CTA)
+constexpr int kToepMaxM = 512;   // M_i
+size_t toeplitz_mu_smem(int N, int M1, int M2);
+cudaError_t run_setup_toeplitz(bccb_solver* s, const void* y_dev);
+cudaError_t run_check_toeplitz(bccb_solver* s, const void* y_dev, const void* c_int);
+cudaError_t toeplitz_pad(bccb_solver* s, const void* c_user, void* c_int);
+cudaError_t toeplitz_crop(bccb_solver* s, const void* c_int, void* c_user);
 // peaks.cu: top-K peaks of every instance of c and their harmonics and angles
 constexpr int kMaxPeakK = 1024;
 cudaError_t run_peaks(bccb_solver* s, const void* c_dev, int K, double rel_thresh, int* idx, double* mag,
