@@ -444,6 +444,40 @@ def run_workload(args):
                 "unit": "instances/s", "ms_per_batch": ms, "peaks_per_instance_median": float(np.median(cnt)),
                 "bytes_read_per_instance_pass": 65536 * 8,
                 "cpu_oracle": {"ms_per_instance": cpu_s * 1e3, "cores": 1, "sample": "16 instances"}}
+    elif args.workload == "toeplitz":
+        # element spacing 0.4 wavelength (gamma != 1/2): Toeplitz Gram, 2L1 x 2L2 circulant embedding
+        B, T, g = min(args.batch, 1024), args.iters, (0.4, 0.4)
+        snaps = [synth.make_snapshot(60000 + i, 32, 32, 256, 128, 128, 8, 10.0, gamma=g) for i in range(B)]
+        insts = [dict(M1=s.M1, M2=s.M2, L1=s.L1, L2=s.L2, mask=s.mask, y=s.y, lam=0.05, lam_is_frac=True)
+                 for s in snaps]
+        stream = torch.cuda.Stream()
+        solver = bccb.BatchSolver(insts, "fista", stream=stream, gamma=g)
+        y = torch.from_numpy(solver.y_host).cuda()
+        c = torch.zeros(solver.total_c, dtype=torch.complex64, device="cuda")
+        torch.cuda.synchronize()
+        bccb.bccb_batch_tune(solver.handle, y, 10, None)
+        bccb.bccb_set_timing(solver.handle, True)
+        solver.solve(y, T, c, check=True)  # warm-up
+        times = []
+        for _ in range(3):
+            solver.solve(y, T, c, check=True)
+            times.append(bccb.bccb_last_timing(solver.handle))
+        res = solver.results()
+        it_ms = statistics.median(t["iterate_ms"] for t in times)
+        su_ms = statistics.median(t["setup_ms"] for t in times)
+        # oracle on a bounded sample: the dense FP64 solve of two snapshots, 100 iterations
+        t0 = time.perf_counter()
+        for s in snaps[:2]:
+            A = oracle.dictionary(s.mask, s.M1, s.M2, s.L1, s.L2, *g)
+            oracle.fista(A, s.y, 0.05 * oracle.lambda_max(A, s.y), 100)
+        cpu = 2 * 100 / (time.perf_counter() - t0)
+        solver.close()
+        line = {"workload": f"gamma = 0.4 array (Toeplitz Gram): {B} snapshots, 32x32 array, N=256, 128x128 grid "
+                            f"(256x256 circulant embedding), 8 off-grid sources, 10 dB, lam=0.05||A^H y||_inf, "
+                            f"FISTA {T} iterations", "value": B * T / (it_ms / 1e3), "unit": "instance-iterations/s",
+                "phases_ms": {"setup": su_ms, "iterate": it_ms}, "kkt_max": float(np.max(res["kkt"])),
+                "cpu_oracle": {"value": cpu, "unit": "instance-iterations/s", "cores": os.cpu_count(),
+                               "sample": "2 snapshots x 100 FISTA iterations, dense FP64 oracle incl. setup"}}
     elif args.workload == "single64":
         s = synth.config_snapshot(1, 0)
         inst = [dict(M1=s.M1, M2=s.M2, L1=s.L1, L2=s.L2, mask=s.mask, y=s.y, lam=0.1, lam_is_frac=True)]
@@ -514,7 +548,7 @@ def main():
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-1e-4 measurement")
     ap.add_argument("--tune-cache", default=None, help="autotuner cache file (default: measure every run)")
     ap.add_argument("--workload", default="batched256",
-                    choices=["batched256", "ragged", "precision1024", "single64", "table1", "peaks"],
+                    choices=["batched256", "ragged", "precision1024", "single64", "table1", "peaks", "toeplitz"],
                     help="batched256 is the benchmark metric; the others print their own line")
     ap.add_argument("--trials", type=int, default=3, help="trials per Table I cell (--workload table1)")
     ap.add_argument("--traffic-bytes", type=float, default=None,

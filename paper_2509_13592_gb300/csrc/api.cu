@@ -597,7 +597,10 @@ int bccb_batch_tune(bccb_solver_t s, const void* y_dev, int probe_iters, const c
   if (need_probe) {
     if (s->algo != BCCB_ADMM) BCCB_CUDA(s, bccb::fista_schedule(s, probe_iters));
     if (!s->d_probe) BCCB_CUDA(s, dalloc(&s->d_probe, s->total_c));
-    BCCB_CUDA(s, bccb::run_setup(s, y_dev));
+    if (s->toeplitz)
+      BCCB_CUDA(s, bccb::run_setup_toeplitz(s, y_dev));
+    else
+      BCCB_CUDA(s, bccb::run_setup(s, y_dev));
     if (cache_path) out = fopen(cache_path, "a");
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;

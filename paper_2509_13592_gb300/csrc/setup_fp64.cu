@@ -516,18 +516,23 @@ __global__ void __launch_bounds__(1024) toep_mu_kernel(const InstDesc* __restric
 
 // Lambda_ext (real part of the embedding's spectrum), q = mu Lambda_ext / L and
 // Bt = mu FFT2(b)/L over the embedded grid (L = its size); the whole spectrum is active
-__global__ void toep_mult_kernel(const InstDesc* __restrict__ desc, const double2* __restrict__ lam_c,
-                                 const double2* __restrict__ fb, const InstParams* __restrict__ par,
-                                 double* lam64, float* mult, float2* bt, double* mult64, double2* bt64,
-                                 FusedInst* fused) {
+__global__ void toep_lam_kernel(const InstDesc* __restrict__ desc, const double2* __restrict__ lam_c, double* lam64) {
+  const InstDesc d = desc[blockIdx.x];
+  const int L = d.L1 * d.L2;
+  for (int cell = blockIdx.y * blockDim.x + threadIdx.x; cell < L; cell += gridDim.y * blockDim.x)
+    lam64[d.g_off + cell] = lam_c[d.g_off + cell].x;
+}
+
+__global__ void toep_mult_kernel(const InstDesc* __restrict__ desc, const double* __restrict__ lam64,
+                                 const double2* __restrict__ fb, const InstParams* __restrict__ par, float* mult,
+                                 float2* bt, double* mult64, double2* bt64, FusedInst* fused) {
   const InstDesc d = desc[blockIdx.x];
   const int L = d.L1 * d.L2;
   const double mu = par[blockIdx.x].mu, inv_L = 1.0 / (double)L;
   for (int cell = blockIdx.y * blockDim.x + threadIdx.x; cell < L; cell += gridDim.y * blockDim.x) {
-    const double lv = lam_c[d.g_off + cell].x;
+    const double lv = lam64[d.g_off + cell];
     const double2 f = fb[d.g_off + cell];
     const double m = mu * lv * inv_L;
-    lam64[d.g_off + cell] = lv;
     mult[d.g_off + cell] = (float)m;
     bt[d.g_off + cell] = make_float2((float)(mu * f.x * inv_L), (float)(mu * f.y * inv_L));
     if (mult64) {
@@ -706,9 +711,18 @@ size_t toeplitz_mu_smem(int N, int M1, int M2) {
 cudaError_t run_setup_toeplitz(bccb_solver* s, const void* y_dev) {
   const dim3 gc = grid_cells(s);
   cudaError_t err;
-  toep_col1_kernel<<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_mask_idx, s->gamma1, s->d_toep_h);
-  toep_col2_kernel<<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_toep_h, s->gamma2, s->d_w64);
-  if ((err = fft2_64(s, s->d_w64, 0)) != cudaSuccess) return err;  // spectrum of the embedding
+  // the mask-only part (the embedding's spectrum and mu) runs once per solver; a solve
+  // being captured into a graph does not count, since its kernels have not run yet
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if ((err = cudaStreamIsCapturing(s->stream, &cs)) != cudaSuccess) return err;
+  const bool mask_part = !s->toep_ready;
+  if (mask_part) {
+    toep_col1_kernel<<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_mask_idx, s->gamma1, s->d_toep_h);
+    toep_col2_kernel<<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_toep_h, s->gamma2, s->d_w64);
+    if ((err = fft2_64(s, s->d_w64, 0)) != cudaSuccess) return err;  // spectrum of the embedding
+    toep_lam_kernel<<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_w64, s->d_lam64);
+    s->launches += 3;
+  }
   if (s->prec == 1)
     toep_b1_kernel<double2><<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_mask_idx,
                                                             static_cast<const double2*>(y_dev), s->gamma1, s->d_toep_h);
@@ -716,26 +730,29 @@ cudaError_t run_setup_toeplitz(bccb_solver* s, const void* y_dev) {
     toep_b1_kernel<float2><<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_mask_idx,
                                                            static_cast<const float2*>(y_dev), s->gamma1, s->d_toep_h);
   toep_b2_kernel<<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_toep_h, s->gamma2, s->d_b64);
-  int maxN = 0, maxM1 = 0, maxM2 = 0;
-  for (const InstDesc& d : s->h_desc) {
-    maxN = std::max(maxN, d.N);
-    maxM1 = std::max(maxM1, d.M1);
-    maxM2 = std::max(maxM2, d.M2);
+  if (mask_part) {
+    int maxN = 0, maxM1 = 0, maxM2 = 0;
+    for (const InstDesc& d : s->h_desc) {
+      maxN = std::max(maxN, d.N);
+      maxM1 = std::max(maxM1, d.M1);
+      maxM2 = std::max(maxM2, d.M2);
+    }
+    const size_t mu_smem = toeplitz_mu_smem(maxN, maxM1, maxM2);
+    if ((err = cudaFuncSetAttribute(toep_mu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mu_smem)) !=
+        cudaSuccess)
+      return err;
+    toep_mu_kernel<<<s->n, 1024, mu_smem, s->stream>>>(s->d_desc, s->d_mask_idx, s->gamma1, s->gamma2, s->d_par);
+    s->launches += 1;
+    if (cs == cudaStreamCaptureStatusNone) s->toep_ready = 1;
   }
-  const size_t mu_smem = toeplitz_mu_smem(maxN, maxM1, maxM2);
-  if ((err = cudaFuncSetAttribute(toep_mu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mu_smem)) !=
-      cudaSuccess)
-    return err;
-  toep_mu_kernel<<<s->n, 1024, mu_smem, s->stream>>>(s->d_desc, s->d_mask_idx,
-                                                                                  s->gamma1, s->gamma2, s->d_par);
   lam_kappa_kernel<<<s->n, kThreads, 0, s->stream>>>(s->d_desc, s->d_b64, s->d_par, s->d_fused, s->algo, s->rho);
   if ((err = cudaMemcpyAsync(s->d_toep_fb, s->d_b64, sizeof(double2) * (size_t)s->total_L, cudaMemcpyDeviceToDevice,
                              s->stream)) != cudaSuccess)
     return err;
   if ((err = fft2_64(s, s->d_toep_fb, 0)) != cudaSuccess) return err;
-  toep_mult_kernel<<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_w64, s->d_toep_fb, s->d_par, s->d_lam64, s->d_mult,
+  toep_mult_kernel<<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_lam64, s->d_toep_fb, s->d_par, s->d_mult,
                                                    s->d_cterm, s->d_mult64, s->d_bt64, s->d_fused);
-  s->launches += 8;
+  s->launches += 4;
   return cudaGetLastError();
 }
 

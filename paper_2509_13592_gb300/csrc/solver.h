@@ -110,6 +110,7 @@ struct bccb_solver {
   void* d_c0int = nullptr;        // embedded warm start (Toeplitz)
   double2* d_toep_h = nullptr;    // FP64 scratch of the Toeplitz setup
   double2* d_toep_fb = nullptr;   // FP64 FFT2 of the zero-padded b (Toeplitz)
+  int toep_ready = 0;             // the embedding's spectrum (d_lam64) and mu are in place
   // iteration engine: 0 = FFT (fused / multi-pass), 1 = dense L x L Gram (dense.cu)
   int method = 0;
   float2* d_gram = nullptr;       // per instance L x L complex64, row-major

@@ -116,3 +116,24 @@ def test_toeplitz_unsupported(lib):
         solver.set_method("dense")
     with pytest.raises(lib.BccbError):
         solver.get(0, torch.zeros(solver.total_c, dtype=torch.float64, device="cuda"))
+
+
+def test_toeplitz_cached_setup_and_tuner(lib):
+    """The mask-only setup (embedding spectrum, mu) runs once per solver; later solves and
+    the autotuner reuse it and give identical results."""
+    import torch
+
+    s = _snap(701, 12, 12, 50, 128, 128)
+    A = _A(s)
+    ref = oracle_run(s, "fista", 100, A=A)
+    solver = lib.BatchSolver([inst(s, ref["lam"])], "fista", gamma=GAM)
+    y = torch.from_numpy(solver.y_host).cuda()
+    c1 = torch.zeros(solver.total_c, dtype=torch.complex64, device="cuda")
+    c2 = torch.zeros_like(c1)
+    solver.solve(y, 100, c1)
+    mu1 = solver.results()["mu"][0]
+    lib.bccb_batch_tune(solver.handle, y, 5, None)
+    solver.solve(y, 100, c2)
+    assert solver.results()["mu"][0] == mu1 == pytest.approx(oracle.step_size(A), rel=1e-12)
+    assert np.array_equal(c1.cpu().numpy(), c2.cpu().numpy())
+    assert_parity(c2.cpu().numpy(), ref, what="toeplitz after tuning")
