@@ -162,7 +162,7 @@ int create_impl(bccb_solver_t* out, const bccb_inst_t* insts, int n, const uint8
       return fail(nullptr, BCCB_ERR_INVALID_ARG, "instance " + std::to_string(i) + ": lam must be >= 0");
     }
     const bool on_chip = prec == BCCB_F32 && q.L1 <= 256 && q.L2 <= 256;
-    if (on_chip && !bccb::fused_lookup(q.L1, q.L2, algo == BCCB_ADMM)) {
+    if (on_chip && !bccb::fused_lookup(q.L1, q.L2, algo == BCCB_ADMM, 0, blk != nullptr)) {
       delete s;
       return fail(nullptr, BCCB_ERR_UNSUPPORTED, "no fused kernel for this grid");
     }
@@ -224,7 +224,7 @@ int create_impl(bccb_solver_t* out, const bccb_inst_t* insts, int n, const uint8
     sc.L2 = o.second.second;
     sc.multipass = !(prec == BCCB_F32 && sc.L1 <= 256 && sc.L2 <= 256);
     if (!sc.multipass)
-      sc.entry = *bccb::fused_lookup(sc.L1, sc.L2, algo == BCCB_ADMM);
+      sc.entry = *bccb::fused_lookup(sc.L1, sc.L2, algo == BCCB_ADMM, 0, blk != nullptr);
     else
       memset(&sc.entry, 0, sizeof(sc.entry));
     any_mp = any_mp || sc.multipass;
@@ -614,7 +614,8 @@ int bccb_batch_tune(bccb_solver_t s, const void* y_dev, int probe_iters, const c
     const auto key = std::make_tuple(c.entry.L1, c.entry.L2, admm);
     auto it = cached.find(key);
     if (it != cached.end()) {
-      if (const bccb::FusedEntry* fe = bccb::fused_lookup(c.entry.L1, c.entry.L2, admm != 0, it->second)) {
+      if (const bccb::FusedEntry* fe =
+              bccb::fused_lookup(c.entry.L1, c.entry.L2, admm != 0, it->second, s->toeplitz != 0)) {
         c.entry = *fe;
         if (c.entry.prepare() != cudaSuccess) status = BCCB_ERR_CUDA;
         continue;
@@ -635,7 +636,7 @@ int bccb_batch_tune(bccb_solver_t s, const void* y_dev, int probe_iters, const c
     float best = 1e30f;
     bccb::FusedEntry best_e = c.entry;
     for (int tile : {8192, 4096}) {
-      const bccb::FusedEntry* fe = bccb::fused_lookup(c.entry.L1, c.entry.L2, admm != 0, tile);
+      const bccb::FusedEntry* fe = bccb::fused_lookup(c.entry.L1, c.entry.L2, admm != 0, tile, s->toeplitz != 0);
       if (!fe || fe->prepare() != cudaSuccess) continue;
       float ms = 0.f;
       bool ok = fe->launch(a, c.count, s->stream) == cudaSuccess;  // warm-up

@@ -18,8 +18,11 @@ namespace bccb {
   fused_entry<L1, BCCB_L2, false>(), fused_entry<L1, BCCB_L2, true>()
 #define BCCB_ENTRIES_HALF(L1)                                                       \
   fused_entry<L1, BCCB_L2, false, 4096>(), fused_entry<L1, BCCB_L2, true, 4096>()
+// ISTA/FISTA on the circulant embedding of a Toeplitz Gram (both sides >= 32)
+#define BCCB_BLOCK(L1) fused_entry<L1, BCCB_L2, false, kFusedTileElems, false, true>()
+#define BCCB_BLOCK_HALF(L1) fused_entry<L1, BCCB_L2, false, 4096, false, true>()
 
-const FusedEntry* BCCB_CAT(fused_lookup_L2_, BCCB_L2)(int L1, bool admm, int tile) {
+const FusedEntry* BCCB_CAT(fused_lookup_L2_, BCCB_L2)(int L1, bool admm, int tile, bool block) {
   static const FusedEntry table[] = {
       BCCB_ENTRIES(16), BCCB_ENTRIES(32), BCCB_ENTRIES(64), BCCB_ENTRIES(128), BCCB_ENTRIES(256),
 #if BCCB_L2 >= 32
@@ -34,9 +37,21 @@ const FusedEntry* BCCB_CAT(fused_lookup_L2_, BCCB_L2)(int L1, bool admm, int til
 #if BCCB_L2 >= 256
       BCCB_ENTRIES_HALF(32),
 #endif
+#if BCCB_L2 >= 32
+      BCCB_BLOCK(32), BCCB_BLOCK(64), BCCB_BLOCK(128), BCCB_BLOCK(256), BCCB_BLOCK_HALF(256),
+#endif
+#if BCCB_L2 >= 64
+      BCCB_BLOCK_HALF(128),
+#endif
+#if BCCB_L2 >= 128
+      BCCB_BLOCK_HALF(64),
+#endif
+#if BCCB_L2 >= 256
+      BCCB_BLOCK_HALF(32),
+#endif
   };
   for (const FusedEntry& e : table)
-    if (e.L1 == L1 && e.admm == (admm ? 1 : 0) && e.tile == tile) return &e;
+    if (e.L1 == L1 && e.admm == (admm ? 1 : 0) && e.tile == tile && e.block == (block ? 1 : 0)) return &e;
   return nullptr;
 }
 

@@ -689,7 +689,9 @@ __device__ __forceinline__ void cluster_barrier() {
 
 // LEARN: honour FusedArgs::scale / ::thresh / ::save (the unrolled network's forward pass);
 // plain solves are compiled without them.
-template <int L1, int L2, bool ADMM, int TILE, bool LEARN = false>
+// BLOCK: the grid is the circulant embedding of a Toeplitz Gram and the update keeps the
+// unknown at 0 outside the instance's block (FusedInst::bl1, bl2); ordinary grids compile without it.
+template <int L1, int L2, bool ADMM, int TILE, bool LEARN = false, bool BLOCK = false>
 __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<L1, L2, ADMM, TILE>::MIN_BLOCKS)
     fused_solve_kernel(const FusedArgs a) {
   using S = FusedShape<L1, L2, ADMM, TILE>;
@@ -756,14 +758,15 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
 
   // The pointwise update of one element after the inverse transform: returns the
   // next iteration's FFT input (z for ISTA/FISTA, z - v for ADMM).
-  const bool blocked = in.bl1 != 0;
   auto update = [&](int row, int e, float2 g, float beta, bool last, float sc, float kap, float2* save_t) -> float2 {
     const int sidx = row * L1 + e;
     if constexpr (!ADMM) {
-      if (blocked && (e >= in.bl1 || crank + C * row >= in.bl2)) {
-        cta.s0[sidx] = make_float2(0.f, 0.f);
-        cta.s1[sidx] = make_float2(0.f, 0.f);
-        return make_float2(0.f, 0.f);
+      if constexpr (BLOCK) {
+        if (e >= in.bl1 || crank + C * row >= in.bl2) {
+          cta.s0[sidx] = make_float2(0.f, 0.f);
+          cta.s1[sidx] = make_float2(0.f, 0.f);
+          return make_float2(0.f, 0.f);
+        }
       }
       const float2 c_old = cta.s0[sidx];
       const float2 x = cta.s1[sidx];  // z^(t)
@@ -872,24 +875,24 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
 // host-side launch table
 // ------------------------------------------------------------------------------------------
 struct FusedEntry {
-  int L1, L2, admm, tile;
+  int L1, L2, admm, tile, block;
   int cluster, threads, smem;
   cudaError_t (*launch)(const FusedArgs&, int n_inst, cudaStream_t);
   cudaError_t (*prepare)();
 };
 
-template <int L1, int L2, bool ADMM, int TILE, bool LEARN = false>
+template <int L1, int L2, bool ADMM, int TILE, bool LEARN = false, bool BLOCK = false>
 cudaError_t fused_prepare() {
   using S = FusedShape<L1, L2, ADMM, TILE>;
-  cudaError_t e = cudaFuncSetAttribute(fused_solve_kernel<L1, L2, ADMM, TILE, LEARN>,
+  cudaError_t e = cudaFuncSetAttribute(fused_solve_kernel<L1, L2, ADMM, TILE, LEARN, BLOCK>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
   if (e == cudaSuccess && S::C > 8)
-    e = cudaFuncSetAttribute(fused_solve_kernel<L1, L2, ADMM, TILE, LEARN>,
+    e = cudaFuncSetAttribute(fused_solve_kernel<L1, L2, ADMM, TILE, LEARN, BLOCK>,
                              cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   return e;
 }
 
-template <int L1, int L2, bool ADMM, int TILE, bool LEARN = false>
+template <int L1, int L2, bool ADMM, int TILE, bool LEARN = false, bool BLOCK = false>
 cudaError_t fused_launch(const FusedArgs& a, int n_inst, cudaStream_t st) {
   using S = FusedShape<L1, L2, ADMM, TILE>;
   if (n_inst <= 0) return cudaSuccess;
@@ -905,14 +908,14 @@ cudaError_t fused_launch(const FusedArgs& a, int n_inst, cudaStream_t st) {
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, fused_solve_kernel<L1, L2, ADMM, TILE, LEARN>, a);
+  return cudaLaunchKernelEx(&cfg, fused_solve_kernel<L1, L2, ADMM, TILE, LEARN, BLOCK>, a);
 }
 
-template <int L1, int L2, bool ADMM, int TILE = kFusedTileElems, bool LEARN = false>
+template <int L1, int L2, bool ADMM, int TILE = kFusedTileElems, bool LEARN = false, bool BLOCK = false>
 FusedEntry fused_entry() {
   using S = FusedShape<L1, L2, ADMM, TILE>;
-  return FusedEntry{L1, L2, ADMM ? 1 : 0, TILE, S::C, S::T, S::SMEM, &fused_launch<L1, L2, ADMM, TILE, LEARN>,
-                    &fused_prepare<L1, L2, ADMM, TILE, LEARN>};
+  return FusedEntry{L1,       L2, ADMM ? 1 : 0, TILE, BLOCK ? 1 : 0, S::C, S::T, S::SMEM,
+                    &fused_launch<L1, L2, ADMM, TILE, LEARN, BLOCK>, &fused_prepare<L1, L2, ADMM, TILE, LEARN, BLOCK>};
 }
 
 }  // namespace bccb

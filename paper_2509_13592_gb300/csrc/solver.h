@@ -136,7 +136,8 @@ cudaError_t prepare_multipass(bccb_solver* s);
 cudaError_t run_multipass(bccb_solver* s, const int* ids, int count, int iters, const void* c0, void* c_out,
                           void* aux, cudaStream_t stream);
 // fused_inst.cu / fused_dispatch.cu: tile 0 = the default 8192-element tile
-const FusedEntry* fused_lookup(int L1, int L2, bool admm, int tile = 0);
+// block: the variant for the circulant embedding of a Toeplitz Gram (ISTA/FISTA, sides >= 32)
+const FusedEntry* fused_lookup(int L1, int L2, bool admm, int tile = 0, bool block = false);
 const AdjointEntry* adjoint_lookup(int L1, int L2);
 // the unrolled network's forward kernel (square grids L1 = L2, FISTA, default tile)
 const FusedEntry* learned_lookup(int L1, int L2);
