@@ -297,8 +297,29 @@ def run_gpu(args, rank, world, local_rank):
                 break
         sub_solver.close()
         per_iter_ms = statistics.median(iterate_ms) / T
+        # the same t_star iterations through the single-instance entry point, one snapshot at a
+        # time (setup, iterations and check of one solve), on the first 8 snapshots
+        single_ms = None
+        if t_star is not None:
+            one_ms = []
+            for d in insts[:8]:
+                one = bccb.BatchSolver([d], "fista", stream=stream)
+                y1 = torch.from_numpy(one.y_host).cuda()
+                c1 = torch.empty(one.total_c, dtype=torch.complex64, device="cuda")
+                one.solve(y1, t_star, c1, check=False)  # warm-up
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                one.solve(y1, t_star, c1, check=False)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                one_ms.append(e0.elapsed_time(e1))
+                one.close()
+            single_ms = statistics.median(one_ms)
+        batched_ms = None if t_star is None else (statistics.median(setup_ms) + t_star * per_iter_ms) / B
         ttt = {"iters": t_star, "sampled_instances": len(sub), "reference_iters": T,
-               "time_ms_full_batch": None if t_star is None else t_star * per_iter_ms}
+               "time_ms_full_batch": None if t_star is None else t_star * per_iter_ms,
+               "batched_ms_per_instance": batched_ms, "single_instance_ms": single_ms,
+               "batched_speedup_vs_single": (single_ms / batched_ms) if (single_ms and batched_ms) else None}
 
     if rank == 0:
         peaks = load_peaks()

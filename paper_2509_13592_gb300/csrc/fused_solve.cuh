@@ -308,18 +308,26 @@ struct FusedCta {
     row = (tid >> 5) * 2 + ((tid & 31) >> 4);
     j = tid & 15;
   }
+  // with j < 16, the padded position of j + 16 i is j + 17 i and that of 16 j + k is 17 j + k:
+  // a per-thread base pointer and compile-time offsets
+  __device__ __forceinline__ float2* sq_col(int row, int j) const { return work + row * P + j; }
+  __device__ __forceinline__ float2* sq_blk(int row, int j) const { return work + row * P + 17 * j; }
 
   // forward first stage from the work rows (used once, before the first iteration)
   __device__ __forceinline__ void sq_fwd1_from_work() {
     int row, j;
     sq_rowj(row, j);
+    float2* const cp = sq_col(row, j);
+    float2* const bp = sq_blk(row, j);
+    (void)cp;
+    (void)bp;
     float2 v[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = work[row * P + pad16(j + 16 * i)];
+    for (int i = 0; i < 16; ++i) v[i] = cp[17 * i];
     __syncwarp();
     Dft<16, false, float2>::run(v);
 #pragma unroll
-    for (int k = 0; k < 16; ++k) work[row * P + pad16(16 * j + k)] = v[k];
+    for (int k = 0; k < 16; ++k) bp[k] = v[k];
     __syncwarp();
   }
 
@@ -327,9 +335,13 @@ struct FusedCta {
   __device__ __forceinline__ void sq_fwd2(int nz) {
     int row, j;
     sq_rowj(row, j);
+    float2* const cp = sq_col(row, j);
+    float2* const bp = sq_blk(row, j);
+    (void)cp;
+    (void)bp;
     float2 v[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = work[row * P + pad16(j + 16 * i)];
+    for (int i = 0; i < 16; ++i) v[i] = cp[17 * i];
     __syncwarp();
 #pragma unroll
     for (int i = 1; i < 16; ++i) v[i] = twmul<false>(v[i], tw256[i * 16 + j]);
@@ -337,7 +349,7 @@ struct FusedCta {
       float2 s0 = v[0];
 #pragma unroll
       for (int i = 1; i < 16; ++i) s0 = cadd(s0, v[i]);
-      work[row * P + pad16(j)] = s0;
+      cp[0] = s0;
     } else if (nz == 2) {
       // outputs k2 = 0 and 1 of the 16-point DFT: sum_i v_i and sum_i v_i W_16^i
       float2 s0 = v[0], s1 = v[0];
@@ -346,13 +358,13 @@ struct FusedCta {
         s0 = cadd(s0, v[i]);
         s1 = cadd(s1, twmul<false>(v[i], tw16[i]));
       }
-      work[row * P + pad16(j)] = s0;
-      work[row * P + pad16(j + 16)] = s1;
+      cp[0] = s0;
+      cp[17] = s1;
     } else {
       Dft<16, false, float2>::run(v);
 #pragma unroll
       for (int k = 0; k < 16; ++k)
-        if (k < nz) work[row * P + pad16(j + 16 * k)] = v[k];
+        if (k < nz) cp[17 * k] = v[k];
     }
     __syncwarp();
   }
@@ -361,21 +373,25 @@ struct FusedCta {
   __device__ __forceinline__ void sq_inv1(int nz) {
     int row, j;
     sq_rowj(row, j);
+    float2* const cp = sq_col(row, j);
+    float2* const bp = sq_blk(row, j);
+    (void)cp;
+    (void)bp;
     float2 v[16];
     if (nz <= 2) {
-      const float2 a = work[row * P + pad16(j)];
-      const float2 b = (nz == 2) ? work[row * P + pad16(j + 16)] : make_float2(0.f, 0.f);
+      const float2 a = cp[0];
+      const float2 b = (nz == 2) ? cp[17] : make_float2(0.f, 0.f);
       __syncwarp();
 #pragma unroll
       for (int k = 0; k < 16; ++k) v[k] = cadd(a, twmul<true>(b, tw16[k]));
     } else {
 #pragma unroll
-      for (int i = 0; i < 16; ++i) v[i] = (i < nz) ? work[row * P + pad16(j + 16 * i)] : make_float2(0.f, 0.f);
+      for (int i = 0; i < 16; ++i) v[i] = (i < nz) ? cp[17 * i] : make_float2(0.f, 0.f);
       __syncwarp();
       Dft<16, true, float2>::run(v);
     }
 #pragma unroll
-    for (int k = 0; k < 16; ++k) work[row * P + pad16(16 * j + k)] = v[k];
+    for (int k = 0; k < 16; ++k) bp[k] = v[k];
     __syncwarp();
   }
 
@@ -389,6 +405,10 @@ struct FusedCta {
   __device__ __forceinline__ void sq_inv2_epi_fwd1(Epi&& epi, bool next, int nz) {
     int row, j;
     sq_rowj(row, j);
+    float2* const cp = sq_col(row, j);
+    float2* const bp = sq_blk(row, j);
+    (void)cp;
+    (void)bp;
     float2 v[16];
     const float2* xr = work + row * P;
     if (nz == 2) {
@@ -403,7 +423,7 @@ struct FusedCta {
       for (int i = 0; i < 16; ++i) v[i] = make_float2(0.f, 0.f);
     } else {
 #pragma unroll
-      for (int i = 0; i < 16; ++i) v[i] = xr[pad16(j + 16 * i)];
+      for (int i = 0; i < 16; ++i) v[i] = xr[j + 17 * i];
     }
     __syncwarp();
 #pragma unroll
@@ -414,7 +434,7 @@ struct FusedCta {
     if (next) {
       Dft<16, false, float2>::run(v);
 #pragma unroll
-      for (int k = 0; k < 16; ++k) work[row * P + pad16(16 * j + k)] = v[k];
+      for (int k = 0; k < 16; ++k) bp[k] = v[k];
     }
     __syncwarp();
   }
