@@ -180,9 +180,9 @@ def run_reference(args, rank, world):
 
 
 # ncu capture of fused_solve_kernel<256,256,FISTA,4096> on 38 instances x 20 iterations:
-# dram__bytes_read.sum = 29.966336 MB, dram__bytes_write.sum = 0
+# dram__bytes_read.sum = 29.96 MB, dram__bytes_write.sum = 7.68 KB
 FUSED_TRAFFIC_TILE = 4096
-FUSED_DRAM_BYTES_PER_INSTANCE = 29.966336e6 / 38
+FUSED_DRAM_BYTES_PER_INSTANCE = (29.96e6 + 7.68e3) / 38
 
 
 def load_peaks():
@@ -489,6 +489,9 @@ def run_workload(args):
         y = torch.from_numpy(solver.y_host).cuda()
         c = torch.zeros(solver.total_c, dtype=torch.complex64, device="cuda")
         torch.cuda.synchronize()
+        bccb.bccb_set_timing(solver.handle, True)
+        solver.solve(y, 1, c, check=False)  # first solve: includes the mask-only setup (spectrum, mu)
+        first_setup = bccb.bccb_last_timing(solver.handle)["setup_ms"]
         bccb.bccb_batch_tune(solver.handle, y, 10, None)
         bccb.bccb_set_timing(solver.handle, True)
         solver.solve(y, T, c, check=True)  # warm-up
@@ -509,7 +512,10 @@ def run_workload(args):
         line = {"workload": f"gamma = 0.4 array (Toeplitz Gram): {B} snapshots, 32x32 array, N=256, 128x128 grid "
                             f"(256x256 circulant embedding), 8 off-grid sources, 10 dB, lam=0.05||A^H y||_inf, "
                             f"FISTA {T} iterations", "value": B * T / (it_ms / 1e3), "unit": "instance-iterations/s",
-                "phases_ms": {"setup": su_ms, "iterate": it_ms}, "kkt_max": float(np.max(res["kkt"])),
+                "phases_ms": {"setup": su_ms, "iterate": it_ms},
+                "setup_first_solve_ms": first_setup,
+                "setup_note": "the mask-only setup (embedding spectrum and mu) runs on a solver's first solve only",
+                "kkt_max": float(np.max(res["kkt"])),
                 "cpu_oracle": {"value": cpu, "unit": "instance-iterations/s", "cores": os.cpu_count(),
                                "sample": "2 snapshots x 100 FISTA iterations, dense FP64 oracle incl. setup"}}
     elif args.workload == "single64":
