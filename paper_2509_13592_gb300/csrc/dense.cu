@@ -107,48 +107,61 @@ __device__ __forceinline__ float2 soft_thr(float2 u, float kappa) {
   return make_float2(u.x * s, u.y * s);
 }
 
+// x is staged through shared memory in chunks of kDenseChunk entries that all eight row
+// warps of the CTA use, so that L2 carries x once per CTA rather than once per row
+constexpr int kDenseChunk = 4096;  // complex entries (32 KB)
+
 template <bool ADMM>
 __global__ void __launch_bounds__(32 * kDenseWarps) dense_iter_kernel(const DenseArgs a) {
+  __shared__ float4 xs[kDenseChunk / 2];
   const InstDesc d = a.desc[blockIdx.y];
   const int L = d.L1 * d.L2;
   const int lane = threadIdx.x & 31;
-  const int row = blockIdx.x * kDenseWarps + (threadIdx.x >> 5);
-  if (row >= L) return;
-  const float4* G = reinterpret_cast<const float4*>(a.gram + a.gram_off[blockIdx.y] + (int64_t)row * L);
+  const int row0 = blockIdx.x * kDenseWarps;
+  if (row0 >= L) return;  // uniform over the CTA
+  const int row = row0 + (threadIdx.x >> 5);
+  const bool live = row < L;
+  const float4* G = reinterpret_cast<const float4*>(a.gram + a.gram_off[blockIdx.y] + (int64_t)(live ? row : row0) * L);
   const float4* X = reinterpret_cast<const float4*>(a.x_in + d.c_off);
-  // two complex entries per 16-byte load; eight loads in flight per lane
+  // two complex entries per 16-byte load
   float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
   const int nq = L >> 1;
-  int q = lane;
-  for (; q + 7 * 32 < nq; q += 8 * 32) {
-    float4 g[8], x[8];
+  for (int base = 0; base < nq; base += kDenseChunk / 2) {
+    const int cq = min(kDenseChunk / 2, nq - base);
+    __syncthreads();
+    for (int q = threadIdx.x; q < cq; q += 32 * kDenseWarps) xs[q] = __ldg(&X[base + q]);
+    __syncthreads();
+    int q = lane;
+    for (; q + 7 * 32 < cq; q += 8 * 32) {
+      float4 g[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) g[k] = __ldg(&G[q + 32 * k]);
+      for (int k = 0; k < 8; ++k) g[k] = __ldg(&G[base + q + 32 * k]);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) x[k] = __ldg(&X[q + 32 * k]);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      acc0.x = fmaf(g[k].x, x[k].x, acc0.x);
-      acc0.x = fmaf(-g[k].y, x[k].y, acc0.x);
-      acc0.y = fmaf(g[k].x, x[k].y, acc0.y);
-      acc0.y = fmaf(g[k].y, x[k].x, acc0.y);
-      acc1.x = fmaf(g[k].z, x[k].z, acc1.x);
-      acc1.x = fmaf(-g[k].w, x[k].w, acc1.x);
-      acc1.y = fmaf(g[k].z, x[k].w, acc1.y);
-      acc1.y = fmaf(g[k].w, x[k].z, acc1.y);
+      for (int k = 0; k < 8; ++k) {
+        const float4 x = xs[q + 32 * k];
+        acc0.x = fmaf(g[k].x, x.x, acc0.x);
+        acc0.x = fmaf(-g[k].y, x.y, acc0.x);
+        acc0.y = fmaf(g[k].x, x.y, acc0.y);
+        acc0.y = fmaf(g[k].y, x.x, acc0.y);
+        acc1.x = fmaf(g[k].z, x.z, acc1.x);
+        acc1.x = fmaf(-g[k].w, x.w, acc1.x);
+        acc1.y = fmaf(g[k].z, x.w, acc1.y);
+        acc1.y = fmaf(g[k].w, x.z, acc1.y);
+      }
+    }
+    for (; q < cq; q += 32) {
+      const float4 g = __ldg(&G[base + q]), x = xs[q];
+      acc0.x = fmaf(g.x, x.x, acc0.x);
+      acc0.x = fmaf(-g.y, x.y, acc0.x);
+      acc0.y = fmaf(g.x, x.y, acc0.y);
+      acc0.y = fmaf(g.y, x.x, acc0.y);
+      acc1.x = fmaf(g.z, x.z, acc1.x);
+      acc1.x = fmaf(-g.w, x.w, acc1.x);
+      acc1.y = fmaf(g.z, x.w, acc1.y);
+      acc1.y = fmaf(g.w, x.z, acc1.y);
     }
   }
-  for (; q < nq; q += 32) {
-    const float4 g = __ldg(&G[q]), x = __ldg(&X[q]);
-    acc0.x = fmaf(g.x, x.x, acc0.x);
-    acc0.x = fmaf(-g.y, x.y, acc0.x);
-    acc0.y = fmaf(g.x, x.y, acc0.y);
-    acc0.y = fmaf(g.y, x.x, acc0.y);
-    acc1.x = fmaf(g.z, x.z, acc1.x);
-    acc1.x = fmaf(-g.w, x.w, acc1.x);
-    acc1.y = fmaf(g.z, x.w, acc1.y);
-    acc1.y = fmaf(g.w, x.z, acc1.y);
-  }
+  if (!live) return;
   float gx = acc0.x + acc1.x, gy = acc0.y + acc1.y;
   for (int o = 16; o > 0; o >>= 1) {
     gx += __shfl_xor_sync(0xffffffffu, gx, o);
