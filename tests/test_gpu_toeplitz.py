@@ -137,3 +137,24 @@ def test_toeplitz_cached_setup_and_tuner(lib):
     assert solver.results()["mu"][0] == mu1 == pytest.approx(oracle.step_size(A), rel=1e-12)
     assert np.array_equal(c1.cpu().numpy(), c2.cpu().numpy())
     assert_parity(c2.cpu().numpy(), ref, what="toeplitz after tuning")
+
+
+def test_toeplitz_host_buffers_and_graph_replay(lib):
+    """The host-buffer entry point and a captured graph give the caller's L1 x L2 packing."""
+    import torch
+
+    snaps = [_snap(801, 8, 8, 20, 32, 32), _snap(802, 10, 6, 24, 64, 32)]
+    refs = [oracle_run(s, "fista", 80, A=_A(s)) for s in snaps]
+    lams = [r["lam"] for r in refs]
+    stream = torch.cuda.Stream()
+    solver = lib.BatchSolver([inst(s, l) for s, l in zip(snaps, lams)], "fista", stream=stream, gamma=GAM)
+    out = np.zeros(solver.total_c, dtype=np.complex64)
+    solver.solve_host(solver.y_host, 80, out)
+    for i, r in enumerate(refs):
+        assert_parity(solver.unpack(out)[i].reshape(-1), r, what=f"host buffers instance {i}")
+    y = torch.from_numpy(solver.y_host).cuda()
+    c = torch.zeros(solver.total_c, dtype=torch.complex64, device="cuda")
+    lib.bccb_batch_capture(solver.handle, y, 80, None, c, None, True)
+    lib.bccb_batch_replay(solver.handle)
+    torch.cuda.synchronize()
+    assert np.array_equal(c.cpu().numpy(), out)
