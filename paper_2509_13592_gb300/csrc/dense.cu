@@ -175,10 +175,14 @@ __global__ void __launch_bounds__(32 * kDenseWarps) dense_iter_kernel(const Dens
     const float mu = (float)a.par[blockIdx.y].mu;
     const float2 u = make_float2(xv.x - mu * gx + k.x, xv.y - mu * gy + k.y);
     const float2 c_old = a.s0[gi];
-    const float2 cn = soft_thr(u, kappa);
+    const float r2 = u.x * u.x + u.y * u.y;
+    const float sc = r2 > kappa * kappa ? 1.0f - kappa * rsqrtf(r2) : 0.0f;
+    const float2 cn = make_float2(u.x * sc, u.y * sc);
     const float beta = a.beta ? a.beta[a.it] : 0.f;
     a.s0[gi] = cn;
-    a.x_out[gi] = make_float2(cn.x + beta * (cn.x - c_old.x), cn.y + beta * (cn.y - c_old.y));
+    // momentum difference from the unrounded product u s (one rounding)
+    const float dx = fmaf(u.x, sc, -c_old.x), dy = fmaf(u.y, sc, -c_old.y);
+    a.x_out[gi] = make_float2(fmaf(beta, dx, cn.x), fmaf(beta, dy, cn.y));
   } else {
     const float sc = (float)(1.0 / (a.rho + (double)L));
     const float2 c = make_float2(xv.x - sc * gx + k.x, xv.y - sc * gy + k.y);

@@ -49,6 +49,12 @@ __device__ __forceinline__ V shrink(V u, typename ScalarOf<V>::T kappa) {
   return cmk<V>((T)0, (T)0);
 }
 
+template <typename T, typename V>
+__device__ __forceinline__ T shrink_scale(V u, T kappa) {
+  const T r2 = u.x * u.x + u.y * u.y;
+  return r2 > kappa * kappa ? (T)1 - kappa / sqrt(r2) : (T)0;
+}
+
 __device__ __forceinline__ int active_cols(int kcols, int L1) { return min(L1, (kcols + 3) & ~3); }
 
 // state <- warm start (or zero); work row input of the first forward row pass is built there too
@@ -107,10 +113,14 @@ __global__ void mp_rows_kernel(MpArgs<V> a) {
       } else if (a.algo != 2) {
         const V c_old = s0[e];
         const V xin = (a.algo == 1) ? s1[e] : c_old;
-        const V cn = shrink(csub(xin, g), kappa);
+        const V un = csub(xin, g);
+        const T sc = shrink_scale(un, kappa);
+        const V cn = cmk<V>(un.x * sc, un.y * sc);
         s0[e] = cn;
         if (a.algo == 1) {
-          next = cadd(cn, cscale(csub(cn, c_old), beta));
+          // momentum difference from the unrounded product u s (see the fused kernel)
+          const T dx = fma(un.x, sc, -c_old.x), dy = fma(un.y, sc, -c_old.y);
+          next = cmk<V>(fma(beta, dx, cn.x), fma(beta, dy, cn.y));
           s1[e] = next;
         } else {
           next = cn;
