@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <map>
 #include <tuple>
+#include <unordered_map>
 #include <string>
 #include <utility>
 #include <vector>
@@ -88,7 +89,7 @@ void release(bccb_solver* s) {
                   s->d_cterm,  s->d_par,      s->d_fused,   s->d_ids,     s->d_beta,    s->d_beta64,
                   s->d_kkt,    s->d_obj,      s->d_red,     s->d_tw32,    s->d_tw64,    s->d_y_stage,
                   s->d_c_stage, s->d_mult64,  s->d_bt64,    s->d_mp_work, s->d_mp_s0,   s->d_mp_s1,
-                  s->d_cint,   s->d_c0int,    s->d_toep_h,  s->d_toep_fb};
+                  s->d_cint,   s->d_c0int,    s->d_toep_h,  s->d_toep_fb, s->d_lam_sel, s->d_lam_src};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -204,8 +205,25 @@ int create_impl(bccb_solver_t* out, const bccb_inst_t* insts, int n, const uint8
                                    blk ? d.u_off + (int64_t)d.bL1 * d.bL2 : q.c_off + (int64_t)q.L1 * q.L2);
     s->max_L1 = std::max(s->max_L1, q.L1);
     s->max_L2 = std::max(s->max_L2, q.L2);
+    s->scat_rows = std::max(s->scat_rows, std::min(q.M2, q.L2));
   }
   s->total_L = g_off;
+
+  // Lambda depends only on (M1, M2, L1, L2, mask): instances that repeat an earlier one's share it
+  std::vector<int> lam_src(n), lam_sel;
+  {
+    std::unordered_map<std::string, int> first_of;
+    for (int i = 0; i < n; ++i) {
+      const bccb_inst_t& q = insts[i];
+      std::string key(reinterpret_cast<const char*>(&q.M1), 4 * sizeof(int));
+      const uint8_t* m = masks_host + q.mask_off;
+      for (int pos = 0; pos < q.M1 * q.M2; ++pos) key.push_back(m[pos] ? '\1' : '\0');
+      auto it = first_of.emplace(std::move(key), i).first;
+      lam_src[i] = it->second;
+      if (it->second == i) lam_sel.push_back(i);
+    }
+  }
+  s->n_lam = (int)lam_sel.size();
   s->total_MM = mm_off;
   s->toeplitz = blk ? 1 : 0;
   s->gamma1 = gamma1;
@@ -271,6 +289,12 @@ int create_impl(bccb_solver_t* out, const bccb_inst_t* insts, int n, const uint8
   CREATE_CUDA(cudaMemcpy(s->d_mask_idx, mask_idx.data(), mask_idx.size() * sizeof(int), cudaMemcpyHostToDevice));
   CREATE_CUDA(cudaMemcpy(s->d_fused, fused.data(), n * sizeof(FusedInst), cudaMemcpyHostToDevice));
   CREATE_CUDA(cudaMemcpy(s->d_ids, ids.data(), n * sizeof(int), cudaMemcpyHostToDevice));
+  if (s->n_lam < n) {
+    CREATE_CUDA(dalloc(&s->d_lam_sel, s->n_lam));
+    CREATE_CUDA(dalloc(&s->d_lam_src, n));
+    CREATE_CUDA(cudaMemcpy(s->d_lam_sel, lam_sel.data(), s->n_lam * sizeof(int), cudaMemcpyHostToDevice));
+    CREATE_CUDA(cudaMemcpy(s->d_lam_src, lam_src.data(), n * sizeof(int), cudaMemcpyHostToDevice));
+  }
   if (prec == BCCB_F64) {
     CREATE_CUDA(dalloc(&s->d_mult64, s->total_L));
     CREATE_CUDA(dalloc(&s->d_bt64, s->total_L));

@@ -158,6 +158,7 @@ extern "C" int bccb_solve_noalloc(int M1, int M2, const uint8_t* mask_dev, int L
   s.device = dev;
   s.max_L1 = L1;
   s.max_L2 = L2;
+  s.scat_rows = std::min(M2, L2);
   s.d_desc = reinterpret_cast<bccb::InstDesc*>(base + kOffDesc);
   s.d_fused = reinterpret_cast<bccb::FusedInst*>(base + kOffFused);
   s.d_ids = reinterpret_cast<int*>(base + kOffIds);

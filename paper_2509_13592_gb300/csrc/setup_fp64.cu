@@ -29,17 +29,23 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// In-place DFT of every row (length L1) of every instance's grid.
-__global__ void fft64_rows_kernel(const InstDesc* __restrict__ desc, double2* base, int inv,
-                                  const double2* __restrict__ tw) {
-  const InstDesc d = desc[blockIdx.x];
+// In-place DFT of every row (length L1) of every instance's grid (of the instances sel lists,
+// when sel is given).  The DFT of a row of zeros is zeros: such a row is left as it is.
+__global__ void fft64_rows_kernel(const InstDesc* __restrict__ desc, const int* __restrict__ sel, double2* base,
+                                  int inv, const double2* __restrict__ tw) {
+  const InstDesc d = desc[sel ? sel[blockIdx.x] : blockIdx.x];
   if ((int)blockIdx.y >= d.L2) return;
   extern __shared__ double2 sm64[];
   double2* x = sm64;
   double2* y = sm64 + d.L1;
   double2* g = base + d.g_off + (int64_t)blockIdx.y * d.L1;
-  for (int e = threadIdx.x; e < d.L1; e += blockDim.x) x[e] = g[e];
-  __syncthreads();
+  int nz = 0;
+  for (int e = threadIdx.x; e < d.L1; e += blockDim.x) {
+    const double2 v = g[e];
+    x[e] = v;
+    nz |= (v.x != 0.0) | (v.y != 0.0);
+  }
+  if (!__syncthreads_or(nz)) return;
   const double2* out = inv ? fft_smem<double2, true>(x, y, d.L1, 1, tw) : fft_smem<double2, false>(x, y, d.L1, 1, tw);
   for (int e = threadIdx.x; e < d.L1; e += blockDim.x) g[e] = out[e];
 }
@@ -47,10 +53,11 @@ __global__ void fft64_rows_kernel(const InstDesc* __restrict__ desc, double2* ba
 // columns staged per block: 8, or fewer so that two L2 x cpb FP64 tiles fit in 128 KB
 int cols_per_block(int max_L2) { return max_L2 <= 512 ? 8 : 4096 / max_L2; }
 
-// In-place DFT of every column (length L2) of every instance's grid, cpb at a time.
-__global__ void fft64_cols_kernel(const InstDesc* __restrict__ desc, double2* base, int inv,
-                                  const double2* __restrict__ tw, int cpb) {
-  const InstDesc d = desc[blockIdx.x];
+// In-place DFT of every column (length L2) of every instance's grid (of the instances sel
+// lists, when sel is given), cpb at a time.
+__global__ void fft64_cols_kernel(const InstDesc* __restrict__ desc, const int* __restrict__ sel, double2* base,
+                                  int inv, const double2* __restrict__ tw, int cpb) {
+  const InstDesc d = desc[sel ? sel[blockIdx.x] : blockIdx.x];
   const int c0 = blockIdx.y * cpb;
   if (c0 >= d.L1) return;
   const int cnt = min(cpb, d.L1 - c0);
@@ -132,20 +139,26 @@ struct SumOp {
 // where s is the signed, folded measurement grid (FFT2(b) = L * s because b is the
 // unnormalised inverse DFT of s).  Entries of Lambda below 1e-9 max Lambda are the
 // round-off of the FP64 DFTs of an exactly zero eigenvalue and are set to 0.
-__global__ void eig_mult_kernel(const InstDesc* __restrict__ desc, const double2* __restrict__ lam_c,
-                                const double2* __restrict__ sgrid, double* lam64, InstParams* par, float* mult,
-                                float2* bt, double* mult64, double2* bt64, FusedInst* fused, int algo, double rho) {
+// With lam_src given, instance i takes Lambda from the grid of instance lam_src[i] (an instance
+// with the same array and grid, whose transform ran in its place).
+__global__ void eig_mult_kernel(const InstDesc* __restrict__ desc, const int* __restrict__ lam_src,
+                                const double2* __restrict__ lam_grid, const double2* __restrict__ sgrid,
+                                double* lam64, InstParams* par, float* mult, float2* bt, double* mult64,
+                                double2* bt64, FusedInst* fused, int algo, double rho) {
   __shared__ double sh[32];
   const InstDesc d = desc[blockIdx.x];
   const int L = d.L1 * d.L2;
+  const double2* lam_c = lam_grid + (lam_src ? desc[lam_src[blockIdx.x]].g_off : d.g_off);
   double top = 0.0;
-  for (int cell = threadIdx.x; cell < L; cell += blockDim.x) top = fmax(top, lam_c[d.g_off + cell].x);
+  for (int cell = threadIdx.x; cell < L; cell += blockDim.x) top = fmax(top, lam_c[cell].x);
   top = block_reduce(top, MaxOp(), sh, 0.0);
   const double mu = 1.0 / top;
   const double inv_L = 1.0 / (double)L;
-  double kc = 0.0;  // 1 + largest Fourier column with a nonzero multiplier or constant term
+  // inv_L is a power of two, so mu inv_L is exact and lv (mu inv_L) rounds like (mu lv) inv_L
+  const double mu_L = mu * inv_L;
+  int kc = 0;  // 1 + largest Fourier column with a nonzero multiplier or constant term
   for (int cell = threadIdx.x; cell < L; cell += blockDim.x) {
-    double lv = lam_c[d.g_off + cell].x;
+    double lv = lam_c[cell].x;
     if (lv < 1e-9 * top) lv = 0.0;
     lam64[d.g_off + cell] = lv;
     const double2 sv = sgrid[d.g_off + cell];
@@ -154,7 +167,7 @@ __global__ void eig_mult_kernel(const InstDesc* __restrict__ desc, const double2
       m = lv / (lv + rho) * inv_L;
       bs = 1.0 / (lv + rho);
     } else {
-      m = mu * lv * inv_L;
+      m = lv * mu_L;
       bs = mu;
     }
     const float mf = (float)m;
@@ -165,13 +178,13 @@ __global__ void eig_mult_kernel(const InstDesc* __restrict__ desc, const double2
       mult64[d.g_off + cell] = m;
       bt64[d.g_off + cell] = make_double2(sv.x * bs, sv.y * bs);
     }
-    if (m != 0.0 || sv.x != 0.0 || sv.y != 0.0) kc = fmax(kc, (double)(cell % d.L1 + 1));
+    if (m != 0.0 || sv.x != 0.0 || sv.y != 0.0) kc = max(kc, (cell & (d.L1 - 1)) + 1);
   }
-  kc = block_reduce(kc, MaxOp(), sh, 0.0);
+  const double kc_all = block_reduce((double)kc, MaxOp(), sh, 0.0);
   if (threadIdx.x == 0) {
     par[blockIdx.x].mu = mu;
     par[blockIdx.x].lam_top = top;
-    fused[blockIdx.x].kcols = (int)kc;
+    fused[blockIdx.x].kcols = (int)kc_all;
   }
 }
 
@@ -181,12 +194,14 @@ __global__ void lam_kappa_kernel(const InstDesc* __restrict__ desc, const double
   __shared__ double sh[32];
   const InstDesc d = desc[blockIdx.x];
   const int L = d.L1 * d.L2;
-  double bmax = 0.0;
+  // max |b| = sqrt(max |b|^2): the correctly rounded square root is monotone, so one root
+  // per instance gives the same value as one per cell
+  double bmax2 = 0.0;
   for (int cell = threadIdx.x; cell < L; cell += blockDim.x) {
     const double2 bv = b64[d.g_off + cell];
-    bmax = fmax(bmax, sqrt(bv.x * bv.x + bv.y * bv.y));
+    bmax2 = fmax(bmax2, bv.x * bv.x + bv.y * bv.y);
   }
-  bmax = block_reduce(bmax, MaxOp(), sh, 0.0);
+  const double bmax = sqrt(block_reduce(bmax2, MaxOp(), sh, 0.0));
   if (threadIdx.x == 0) {
     const double mu = par[blockIdx.x].mu;
     const double lam = d.lam_is_frac ? d.lam * bmax : d.lam;
@@ -251,24 +266,28 @@ __global__ void kkt_final_kernel(const InstDesc* __restrict__ desc, const double
   const int L = d.L1 * d.L2;
   const double lam = par[blockIdx.x].lam;
   const double inv_L = 1.0 / (double)L;
-  double worst = 0.0, l1 = 0.0;
+  // On a zero entry the violation max(|r| - lam, 0) is a monotone function of |r|^2 (each step
+  // correctly rounded), so the largest |r|^2 over the zero entries gives their largest violation:
+  // one square root per thread instead of one per cell.
+  double worst = 0.0, l1 = 0.0, r2_zero = 0.0;
   for (int cell = threadIdx.x; cell < L; cell += blockDim.x) {
     const double2 bv = b64[d.g_off + cell];
     const double2 gv = gc[d.g_off + cell];
     const double rx = bv.x - gv.x * inv_L, ry = bv.y - gv.y * inv_L;
     const C cv = c[d.c_off + cell];
     const double cx = cv.x, cy = cv.y;
-    const double mag = sqrt(cx * cx + cy * cy);
-    double viol;
-    if (mag > 0.0) {
-      const double ex = rx - lam * cx / mag, ey = ry - lam * cy / mag;
-      viol = sqrt(ex * ex + ey * ey);
-    } else {
-      viol = fmax(sqrt(rx * rx + ry * ry) - lam, 0.0);
+    if (cx != 0.0 || cy != 0.0) {
+      const double mag = sqrt(cx * cx + cy * cy);
+      l1 += mag;
+      if (mag > 0.0) {
+        const double ex = rx - lam * cx / mag, ey = ry - lam * cy / mag;
+        worst = fmax(worst, sqrt(ex * ex + ey * ey));
+        continue;
+      }
     }
-    worst = fmax(worst, viol);
-    l1 += mag;
+    r2_zero = fmax(r2_zero, rx * rx + ry * ry);
   }
+  worst = fmax(worst, fmax(sqrt(r2_zero) - lam, 0.0));
   worst = block_reduce(worst, MaxOp(), sh, 0.0);
   l1 = block_reduce(l1, SumOp(), sh, 0.0);
   if (threadIdx.x == 0) {
@@ -297,14 +316,18 @@ dim3 grid_cells(const bccb_solver* s) {
   return dim3((unsigned)s->n, (unsigned)(blocks < 64 ? blocks : 64));
 }
 
-cudaError_t fft2_64(bccb_solver* s, double2* grid, int inv) {
+// FFT2 of every instance's grid, or of the `count` instances listed in sel; rows > 0 says that
+// every row from `rows` on is zero in each grid (the rows pass then launches only the others).
+cudaError_t fft2_64(bccb_solver* s, double2* grid, int inv, int rows = 0, const int* sel = nullptr, int count = 0) {
   s->launches += 2;
+  const int nb = sel ? count : s->n;
+  const int ry = rows > 0 ? std::min(rows, s->max_L2) : s->max_L2;
   const size_t smr = (size_t)2 * s->max_L1 * sizeof(double2);
-  fft64_rows_kernel<<<dim3(s->n, s->max_L2), 128, smr, s->stream>>>(s->d_desc, grid, inv, s->d_tw64);
+  fft64_rows_kernel<<<dim3(nb, ry), 128, smr, s->stream>>>(s->d_desc, sel, grid, inv, s->d_tw64);
   const int cpb = cols_per_block(s->max_L2);
   const size_t smc = (size_t)2 * s->max_L2 * cpb * sizeof(double2);
-  fft64_cols_kernel<<<dim3(s->n, (s->max_L1 + cpb - 1) / cpb), 128, smc, s->stream>>>(s->d_desc, grid, inv,
-                                                                                        s->d_tw64, cpb);
+  fft64_cols_kernel<<<dim3(nb, (s->max_L1 + cpb - 1) / cpb), 128, smc, s->stream>>>(s->d_desc, sel, grid, inv,
+                                                                                     s->d_tw64, cpb);
   return cudaGetLastError();
 }
 
@@ -665,13 +688,17 @@ cudaError_t run_setup(bccb_solver* s, const void* y_dev) {
     scatter_kernel<float2><<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_mask_idx,
                                                            static_cast<const float2*>(y_dev), s->d_w64, s->d_b64);
   s->launches += 3;  // scatter, eig_mult, lam_kappa
+  // Both scattered grids are zero from row min(M2, L2) on.  Lambda depends on the mask alone:
+  // an instance whose array and grid repeat an earlier instance's takes that one's (lam_src),
+  // and the two transforms run only over the distinct ones (lam_sel).
   cudaError_t err;
-  if ((err = fft2_64(s, s->d_w64, 1)) != cudaSuccess) return err;  // first column of the Gram
-  if ((err = fft2_64(s, s->d_w64, 0)) != cudaSuccess) return err;  // Lambda (eq:lambda)
-  eig_mult_kernel<<<s->n, kThreads, 0, s->stream>>>(s->d_desc, s->d_w64, s->d_b64, s->d_lam64, s->d_par,
-                                                     s->d_mult, s->d_cterm, s->d_mult64, s->d_bt64, s->d_fused,
-                                                     s->algo, s->rho);
-  if ((err = fft2_64(s, s->d_b64, 1)) != cudaSuccess) return err;  // b = A^H y
+  if ((err = fft2_64(s, s->d_w64, 1, s->scat_rows, s->d_lam_sel, s->n_lam)) != cudaSuccess)
+    return err;  // first column of the Gram
+  if ((err = fft2_64(s, s->d_w64, 0, 0, s->d_lam_sel, s->n_lam)) != cudaSuccess) return err;  // Lambda (eq:lambda)
+  eig_mult_kernel<<<s->n, kThreads, 0, s->stream>>>(s->d_desc, s->d_lam_src, s->d_w64, s->d_b64, s->d_lam64,
+                                                     s->d_par, s->d_mult, s->d_cterm, s->d_mult64, s->d_bt64,
+                                                     s->d_fused, s->algo, s->rho);
+  if ((err = fft2_64(s, s->d_b64, 1, s->scat_rows)) != cudaSuccess) return err;  // b = A^H y
   lam_kappa_kernel<<<s->n, kThreads, 0, s->stream>>>(s->d_desc, s->d_b64, s->d_par, s->d_fused, s->algo, s->rho);
   return cudaGetLastError();
 }

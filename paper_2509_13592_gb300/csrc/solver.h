@@ -56,6 +56,10 @@ struct bccb_solver {
   int64_t total_y = 0;
   int64_t total_c = 0;
   int max_L1 = 0, max_L2 = 0;
+  int scat_rows = 0;              // max over instances of min(M2, L2): rows of a scattered grid that may be nonzero
+  int n_lam = 0;                  // instances with distinct (array, grid): Lambda transforms per setup
+  int* d_lam_sel = nullptr;       // their ids (null when every instance is distinct)
+  int* d_lam_src = nullptr;       // per instance, the id whose Lambda it shares (null likewise)
   std::vector<bccb::InstDesc> h_desc;
   std::vector<bccb::ShapeClass> classes;
 

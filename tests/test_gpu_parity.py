@@ -43,6 +43,34 @@ def test_setup_lambda_b_mu(lib, M1, M2, N, L1, L2):
     assert abs(run["res"]["mu"][0] * oracle.step_size(A) ** -1 - 1.0) <= 1e-12
 
 
+def test_shared_mask_batch_shares_lambda(lib):
+    """Instances with the same array and grid take Lambda from one transform: each one's
+    Lambda, mu and solution equal those of a one-instance solve bit for bit, and instances
+    on another mask or grid keep their own."""
+    import torch
+
+    rng = np.random.Generator(np.random.PCG64(77))
+    shared = synth.make_mask(rng, 16, 12, 60)
+    other = synth.make_mask(rng, 16, 12, 60)
+    snaps = [_snap(700 + i, 16, 12, 60, 64, 32, mask=m, K=3, snr=20.0)
+             for i, m in enumerate([shared, shared, other, shared, other])]
+    snaps.append(_snap(706, 16, 12, 60, 32, 32, mask=shared, K=2, snr=20.0))  # same mask, other grid
+    refs = [oracle_run(s, "fista", 60) for s in snaps]
+    run = gpu_run(lib, snaps, [r["lam"] for r in refs], "fista", 60)
+    lam_all = torch.zeros(run["solver"].total_c, dtype=torch.float64, device="cuda")
+    run["solver"].get(lib.GET_LAMBDA, lam_all)
+    lam_all = lam_all.cpu().numpy()
+    for i, (s, r) in enumerate(zip(snaps, refs)):
+        assert_parity(run["c"][i], r, what=f"shared-mask batch instance {i}")
+        one = gpu_run(lib, [s], [r["lam"]], "fista", 60)
+        lam_one = torch.zeros(s.L1 * s.L2, dtype=torch.float64, device="cuda")
+        one["solver"].get(lib.GET_LAMBDA, lam_one)
+        o, L1, L2 = run["solver"].offsets[i]
+        assert np.array_equal(lam_all[o:o + L1 * L2], lam_one.cpu().numpy()), f"Lambda of instance {i}"
+        assert run["res"]["mu"][i] == one["res"]["mu"][0]
+        assert run["res"]["kkt"][i] == pytest.approx(one["res"]["kkt"][0], rel=1e-6, abs=1e-9)
+
+
 def test_lambda_fraction_of_lmax(lib):
     s = synth.config_snapshot(1, 3)
     A = oracle.dictionary(s.mask, s.M1, s.M2, s.L1, s.L2)
