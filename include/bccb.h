@@ -125,7 +125,12 @@ int bccb_batch_solve(bccb_solver_t s, const void* y_dev, int iters, const void* 
                      void* aux_out_dev, int check);
 
 /* bccb_batch_solve with HOST buffers: copies y to the device, solves, copies c
- * back; synchronises.  y_host / c_out_host use the same packing as above. */
+ * back; synchronises.  y_host / c_out_host use the same packing as above.  A batch
+ * of one on-chip shape class (FP32, gamma = 1/2, FFT method) with at least 64
+ * instances is solved as 8 launches of consecutive instances; each launch's
+ * solutions are copied back while the later ones run, when they fill a contiguous
+ * range of c_out (with pageable c_out_host the copies still follow all GPU work).
+ * On an error no copy into c_out_host is still in flight when the call returns. */
 int bccb_batch_solve_host(bccb_solver_t s, const void* y_host, int iters, void* c_out_host, int check);
 
 /* Per-instance scalars of the last solve, copied to host arrays of length n (each

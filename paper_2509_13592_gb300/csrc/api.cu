@@ -63,9 +63,18 @@ void release_streams(bccb_solver* s) {
   if (s->fork) cudaEventDestroy(s->fork);
   if (s->graph) cudaGraphExecDestroy(s->graph);
   if (s->d_probe) cudaFree(s->d_probe);
+  for (cudaStream_t st : s->chunk_streams)
+    if (st) cudaStreamDestroy(st);
+  if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+  for (cudaEvent_t ev : s->chunk_done) cudaEventDestroy(ev);
+  if (s->chunk_fork) cudaEventDestroy(s->chunk_fork);
+  if (s->copies_done) cudaEventDestroy(s->copies_done);
   s->class_streams.clear();
   s->class_done.clear();
   s->fork = nullptr;
+  s->chunk_streams[0] = s->chunk_streams[1] = s->copy_stream = nullptr;
+  s->chunk_done.clear();
+  s->chunk_fork = s->copies_done = nullptr;
   s->graph = nullptr;
   s->d_probe = nullptr;
 }
@@ -289,6 +298,7 @@ int create_impl(bccb_solver_t* out, const bccb_inst_t* insts, int n, const uint8
   CREATE_CUDA(cudaMemcpy(s->d_mask_idx, mask_idx.data(), mask_idx.size() * sizeof(int), cudaMemcpyHostToDevice));
   CREATE_CUDA(cudaMemcpy(s->d_fused, fused.data(), n * sizeof(FusedInst), cudaMemcpyHostToDevice));
   CREATE_CUDA(cudaMemcpy(s->d_ids, ids.data(), n * sizeof(int), cudaMemcpyHostToDevice));
+  s->h_ids = ids;
   if (s->n_lam < n) {
     CREATE_CUDA(dalloc(&s->d_lam_sel, s->n_lam));
     CREATE_CUDA(dalloc(&s->d_lam_src, n));
@@ -322,6 +332,181 @@ int create_impl(bccb_solver_t* out, const bccb_inst_t* insts, int n, const uint8
   }
 #undef CREATE_CUDA
   *out = s;
+  return BCCB_OK;
+}
+
+// A chunk of the single fused shape class: positions [first, first + count) of its
+// class-sorted ids, whose solutions fill the complex range [lo, hi) of c_out exactly.
+struct Chunk {
+  int first, count;
+  int64_t lo, hi;
+};
+
+// Splits the batch for a streamed host-buffer solve.  Only a solver with one fused shape class
+// (FFT method, gamma = 1/2) and at least 64 instances is split, into 8 chunks, and only when
+// each chunk's instances tile a contiguous range of c_out; otherwise chunks stays empty.
+bool plan_chunks(bccb_solver* s, std::vector<Chunk>& chunks) {
+  chunks.clear();
+  if (s->toeplitz || s->method != BCCB_FFT || s->classes.size() != 1 || s->classes[0].multipass) return false;
+  const bccb::ShapeClass& c = s->classes[0];
+  constexpr int kChunks = 8;
+  if (c.count < 8 * kChunks) return false;
+  for (int j = 0; j < kChunks; ++j) {
+    Chunk k;
+    k.first = (int)((int64_t)c.count * j / kChunks);
+    k.count = (int)((int64_t)c.count * (j + 1) / kChunks) - k.first;
+    k.lo = INT64_MAX;
+    k.hi = 0;
+    int64_t cells = 0;
+    for (int q = 0; q < k.count; ++q) {
+      const InstDesc& d = s->h_desc[s->h_ids[c.first + k.first + q]];
+      const int64_t L = (int64_t)d.L1 * d.L2;
+      k.lo = std::min(k.lo, d.c_off);
+      k.hi = std::max(k.hi, d.c_off + L);
+      cells += L;
+    }
+    if (k.hi - k.lo != cells) {
+      chunks.clear();
+      return false;
+    }
+    chunks.push_back(k);
+  }
+  if (!s->copy_stream) {
+    for (cudaStream_t& st : s->chunk_streams)
+      if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) st = nullptr;
+    if (cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) != cudaSuccess) s->copy_stream = nullptr;
+    cudaEventCreateWithFlags(&s->chunk_fork, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&s->copies_done, cudaEventDisableTiming);
+  }
+  while (s->chunk_done.size() < chunks.size()) {
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) break;
+    s->chunk_done.push_back(ev);
+  }
+  if (!s->chunk_streams[0] || !s->chunk_streams[1] || !s->copy_stream || !s->chunk_fork || !s->copies_done ||
+      s->chunk_done.size() < chunks.size()) {
+    chunks.clear();
+    return false;
+  }
+  return true;
+}
+
+// The whole solve (bccb_batch_solve); with host_out it also copies the solutions to that host
+// buffer on the solver's stream (the caller synchronises).
+int solve_impl(bccb_solver_t s, const void* y_dev, int iters, const void* c0_dev, void* c_out_dev,
+               void* aux_out_dev, int check, void* host_out) {
+  if (!s) return fail(nullptr, BCCB_ERR_INVALID_ARG, "solver is NULL");
+
+  s->last_error.clear();
+  if (!y_dev || !c_out_dev) return fail(s, BCCB_ERR_INVALID_ARG, "y and c_out must be device pointers");
+  if (iters < 1) return fail(s, BCCB_ERR_INVALID_ARG, "iters must be >= 1");
+  BCCB_CUDA(s, cudaSetDevice(s->device));
+  s->launches = 0;
+  if (s->timing) BCCB_CUDA(s, record_timing(s, 0));
+  if (s->algo != BCCB_ADMM) BCCB_CUDA(s, bccb::fista_schedule(s, iters));
+  const void* y = y_dev;
+  // a Toeplitz solver iterates on embedded grids: warm start padded in, result cropped out
+  const void* k_c0 = c0_dev;
+  void* k_out = c_out_dev;
+  if (s->toeplitz) {
+    BCCB_CUDA(s, bccb::run_setup_toeplitz(s, y));
+    if (c0_dev) {
+      BCCB_CUDA(s, bccb::toeplitz_pad(s, c0_dev, s->d_c0int));
+      k_c0 = s->d_c0int;
+    }
+    k_out = s->d_cint;
+  } else {
+    BCCB_CUDA(s, bccb::run_setup(s, y));
+  }
+  if (s->timing) BCCB_CUDA(s, record_timing(s, 1));
+  FusedArgs a{};
+  a.insts = s->d_fused;
+  a.beta = (s->algo != BCCB_ADMM) ? s->d_beta : nullptr;
+  a.twiddle = s->d_tw32;
+  a.mult = s->d_mult;
+  a.bt = s->d_cterm;
+  a.c0 = reinterpret_cast<const float2*>(k_c0);
+  a.c_out = reinterpret_cast<float2*>(k_out);
+  a.aux_out = (s->algo == BCCB_ADMM) ? reinterpret_cast<float2*>(aux_out_dev) : nullptr;
+  a.iters = iters;
+  a.pad_ = 0;
+  if (s->method == BCCB_DENSE) {
+    BCCB_CUDA(s, bccb::run_dense(s, iters, c0_dev, c_out_dev, s->algo == BCCB_ADMM ? aux_out_dev : nullptr));
+    if (s->timing) BCCB_CUDA(s, record_timing(s, 2));
+    if (check) BCCB_CUDA(s, bccb::run_check(s, y, c_out_dev));
+    if (s->timing) BCCB_CUDA(s, record_timing(s, 3));
+    if (host_out) {
+      const size_t vb = s->prec == BCCB_F64 ? sizeof(double2) : sizeof(float2);
+      BCCB_CUDA(s, cudaMemcpyAsync(host_out, c_out_dev, s->total_u * vb, cudaMemcpyDeviceToHost, s->stream));
+    }
+    s->last_checked = check != 0;
+    return BCCB_OK;
+  }
+  auto launch_class = [&](const bccb::ShapeClass& c, cudaStream_t st) -> cudaError_t {
+    if (c.multipass)
+      return bccb::run_multipass(s, s->d_ids + c.first, c.count, iters, k_c0, k_out,
+                                 s->algo == BCCB_ADMM ? aux_out_dev : nullptr, st);
+    a.ids = s->d_ids + c.first;
+    s->launches += 1;
+    return c.entry.launch(a, c.count, st);
+  };
+  std::vector<Chunk> chunks;
+  if (host_out && plan_chunks(s, chunks)) {
+    // chunks alternate between two streams, so that one chunk's last wave overlaps the next
+    // one's first; their copies to the host are queued after the check (below)
+    const bccb::ShapeClass& c = s->classes[0];
+    BCCB_CUDA(s, cudaEventRecord(s->chunk_fork, s->stream));
+    for (cudaStream_t st : s->chunk_streams) BCCB_CUDA(s, cudaStreamWaitEvent(st, s->chunk_fork, 0));
+    for (size_t j = 0; j < chunks.size(); ++j) {
+      cudaStream_t st = s->chunk_streams[j & 1];
+      a.ids = s->d_ids + c.first + chunks[j].first;
+      s->launches += 1;
+      BCCB_CUDA(s, c.entry.launch(a, chunks[j].count, st));
+      BCCB_CUDA(s, cudaEventRecord(s->chunk_done[j], st));
+    }
+    for (size_t j = chunks.size() - 2; j < chunks.size(); ++j)
+      BCCB_CUDA(s, cudaStreamWaitEvent(s->stream, s->chunk_done[j], 0));
+  } else if (s->classes.size() == 1) {
+    BCCB_CUDA(s, launch_class(s->classes[0], s->stream));
+  } else {
+    // one stream per shape class, forked from and joined back to the solver's stream
+    BCCB_CUDA(s, cudaEventRecord(s->fork, s->stream));
+    for (size_t k = 0; k < s->classes.size(); ++k) {
+      BCCB_CUDA(s, cudaStreamWaitEvent(s->class_streams[k], s->fork, 0));
+      BCCB_CUDA(s, launch_class(s->classes[k], s->class_streams[k]));
+      BCCB_CUDA(s, cudaEventRecord(s->class_done[k], s->class_streams[k]));
+      BCCB_CUDA(s, cudaStreamWaitEvent(s->stream, s->class_done[k], 0));
+    }
+  }
+  if (s->toeplitz) BCCB_CUDA(s, bccb::toeplitz_crop(s, s->d_cint, c_out_dev));
+  if (s->timing) BCCB_CUDA(s, record_timing(s, 2));
+  if (check) {
+    if (s->toeplitz)
+      BCCB_CUDA(s, bccb::run_check_toeplitz(s, y, s->d_cint));
+    else
+      BCCB_CUDA(s, bccb::run_check(s, y, c_out_dev));
+  }
+  if (s->timing) BCCB_CUDA(s, record_timing(s, 3));
+  if (host_out) {
+    const size_t vb = s->prec == BCCB_F64 ? sizeof(double2) : sizeof(float2);
+    if (chunks.empty()) {
+      BCCB_CUDA(s, cudaMemcpyAsync(host_out, c_out_dev, s->total_u * vb, cudaMemcpyDeviceToHost, s->stream));
+    } else {
+      // each chunk's copy waits only for that chunk: with pinned memory the copies overlap the
+      // later chunks and the check (all GPU work is queued before the first copy, which with
+      // pageable memory returns only when done)
+      for (size_t j = 0; j < chunks.size(); ++j) {
+        const Chunk& k = chunks[j];
+        BCCB_CUDA(s, cudaStreamWaitEvent(s->copy_stream, s->chunk_done[j], 0));
+        BCCB_CUDA(s, cudaMemcpyAsync(static_cast<char*>(host_out) + k.lo * vb,
+                                     static_cast<const char*>(c_out_dev) + k.lo * vb, (size_t)(k.hi - k.lo) * vb,
+                                     cudaMemcpyDeviceToHost, s->copy_stream));
+      }
+      BCCB_CUDA(s, cudaEventRecord(s->copies_done, s->copy_stream));
+      BCCB_CUDA(s, cudaStreamWaitEvent(s->stream, s->copies_done, 0));
+    }
+  }
+  s->last_checked = check != 0;
   return BCCB_OK;
 }
 
@@ -377,80 +562,9 @@ int bccb_batch_create_gamma(bccb_solver_t* out, const bccb_inst_t* insts, int n,
 
 int bccb_batch_solve(bccb_solver_t s, const void* y_dev, int iters, const void* c0_dev, void* c_out_dev,
                      void* aux_out_dev, int check) {
-  if (!s) return fail(nullptr, BCCB_ERR_INVALID_ARG, "solver is NULL");
-  s->last_error.clear();
-  if (!y_dev || !c_out_dev) return fail(s, BCCB_ERR_INVALID_ARG, "y and c_out must be device pointers");
-  if (iters < 1) return fail(s, BCCB_ERR_INVALID_ARG, "iters must be >= 1");
-  BCCB_CUDA(s, cudaSetDevice(s->device));
-  s->launches = 0;
-  if (s->timing) BCCB_CUDA(s, record_timing(s, 0));
-  if (s->algo != BCCB_ADMM) BCCB_CUDA(s, bccb::fista_schedule(s, iters));
-  const void* y = y_dev;
-  // a Toeplitz solver iterates on embedded grids: warm start padded in, result cropped out
-  const void* k_c0 = c0_dev;
-  void* k_out = c_out_dev;
-  if (s->toeplitz) {
-    BCCB_CUDA(s, bccb::run_setup_toeplitz(s, y));
-    if (c0_dev) {
-      BCCB_CUDA(s, bccb::toeplitz_pad(s, c0_dev, s->d_c0int));
-      k_c0 = s->d_c0int;
-    }
-    k_out = s->d_cint;
-  } else {
-    BCCB_CUDA(s, bccb::run_setup(s, y));
-  }
-  if (s->timing) BCCB_CUDA(s, record_timing(s, 1));
-  FusedArgs a{};
-  a.insts = s->d_fused;
-  a.beta = (s->algo != BCCB_ADMM) ? s->d_beta : nullptr;
-  a.twiddle = s->d_tw32;
-  a.mult = s->d_mult;
-  a.bt = s->d_cterm;
-  a.c0 = reinterpret_cast<const float2*>(k_c0);
-  a.c_out = reinterpret_cast<float2*>(k_out);
-  a.aux_out = (s->algo == BCCB_ADMM) ? reinterpret_cast<float2*>(aux_out_dev) : nullptr;
-  a.iters = iters;
-  a.pad_ = 0;
-  if (s->method == BCCB_DENSE) {
-    BCCB_CUDA(s, bccb::run_dense(s, iters, c0_dev, c_out_dev, s->algo == BCCB_ADMM ? aux_out_dev : nullptr));
-    if (s->timing) BCCB_CUDA(s, record_timing(s, 2));
-    if (check) BCCB_CUDA(s, bccb::run_check(s, y, c_out_dev));
-    if (s->timing) BCCB_CUDA(s, record_timing(s, 3));
-    s->last_checked = check != 0;
-    return BCCB_OK;
-  }
-  auto launch_class = [&](const bccb::ShapeClass& c, cudaStream_t st) -> cudaError_t {
-    if (c.multipass)
-      return bccb::run_multipass(s, s->d_ids + c.first, c.count, iters, k_c0, k_out,
-                                 s->algo == BCCB_ADMM ? aux_out_dev : nullptr, st);
-    a.ids = s->d_ids + c.first;
-    s->launches += 1;
-    return c.entry.launch(a, c.count, st);
-  };
-  if (s->classes.size() == 1) {
-    BCCB_CUDA(s, launch_class(s->classes[0], s->stream));
-  } else {
-    // one stream per shape class, forked from and joined back to the solver's stream
-    BCCB_CUDA(s, cudaEventRecord(s->fork, s->stream));
-    for (size_t k = 0; k < s->classes.size(); ++k) {
-      BCCB_CUDA(s, cudaStreamWaitEvent(s->class_streams[k], s->fork, 0));
-      BCCB_CUDA(s, launch_class(s->classes[k], s->class_streams[k]));
-      BCCB_CUDA(s, cudaEventRecord(s->class_done[k], s->class_streams[k]));
-      BCCB_CUDA(s, cudaStreamWaitEvent(s->stream, s->class_done[k], 0));
-    }
-  }
-  if (s->toeplitz) BCCB_CUDA(s, bccb::toeplitz_crop(s, s->d_cint, c_out_dev));
-  if (s->timing) BCCB_CUDA(s, record_timing(s, 2));
-  if (check) {
-    if (s->toeplitz)
-      BCCB_CUDA(s, bccb::run_check_toeplitz(s, y, s->d_cint));
-    else
-      BCCB_CUDA(s, bccb::run_check(s, y, c_out_dev));
-  }
-  if (s->timing) BCCB_CUDA(s, record_timing(s, 3));
-  s->last_checked = check != 0;
-  return BCCB_OK;
+  return solve_impl(s, y_dev, iters, c0_dev, c_out_dev, aux_out_dev, check, nullptr);
 }
+
 
 int bccb_batch_solve_host(bccb_solver_t s, const void* y_host, int iters, void* c_out_host, int check) {
   if (!s) return fail(nullptr, BCCB_ERR_INVALID_ARG, "solver is NULL");
@@ -460,9 +574,12 @@ int bccb_batch_solve_host(bccb_solver_t s, const void* y_host, int iters, void* 
   if (!s->d_y_stage) BCCB_CUDA(s, dalloc(&s->d_y_stage, s->total_y * vb / sizeof(float2)));
   if (!s->d_c_stage) BCCB_CUDA(s, dalloc(&s->d_c_stage, s->total_u * vb / sizeof(float2)));
   BCCB_CUDA(s, cudaMemcpyAsync(s->d_y_stage, y_host, s->total_y * vb, cudaMemcpyHostToDevice, s->stream));
-  int st = bccb_batch_solve(s, s->d_y_stage, iters, nullptr, s->d_c_stage, nullptr, check);
-  if (st != BCCB_OK) return st;
-  BCCB_CUDA(s, cudaMemcpyAsync(c_out_host, s->d_c_stage, s->total_u * vb, cudaMemcpyDeviceToHost, s->stream));
+  int st = solve_impl(s, s->d_y_stage, iters, nullptr, s->d_c_stage, nullptr, check, c_out_host);
+  if (st != BCCB_OK) {
+    cudaStreamSynchronize(s->stream);  // no copy into the caller's buffer outlives the call
+    if (s->copy_stream) cudaStreamSynchronize(s->copy_stream);
+    return st;
+  }
   BCCB_CUDA(s, cudaStreamSynchronize(s->stream));
   return BCCB_OK;
 }

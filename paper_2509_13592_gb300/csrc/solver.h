@@ -95,6 +95,14 @@ struct bccb_solver {
   std::vector<cudaStream_t> class_streams;
   std::vector<cudaEvent_t> class_done;
   cudaEvent_t fork = nullptr;
+  // host-buffer solve of one fused shape class: chunks of instances on two streams, each
+  // chunk's results copied to the host on copy_stream as soon as the chunk ends
+  std::vector<int> h_ids;                      // class-sorted instance ids (as d_ids)
+  cudaStream_t chunk_streams[2] = {nullptr, nullptr};
+  cudaStream_t copy_stream = nullptr;
+  std::vector<cudaEvent_t> chunk_done;
+  cudaEvent_t chunk_fork = nullptr;
+  cudaEvent_t copies_done = nullptr;
   // captured solve (bccb_batch_capture / bccb_batch_replay)
   cudaGraphExec_t graph = nullptr;
   // probe output for the autotuner

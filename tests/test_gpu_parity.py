@@ -301,6 +301,58 @@ def test_host_entry_point_matches_device(lib):
     np.testing.assert_array_equal(np.concatenate(dev["c"]), out)
 
 
+def _solve_dev_and_host(lib, insts, masks, y, total_c, iters):
+    """Device solve and host-buffer solves (pageable numpy, pinned torch) on one solver."""
+    import torch
+
+    h = lib.bccb_batch_create(insts, masks, lib.ALGOS["fista"])
+    try:
+        y_dev = torch.from_numpy(y).cuda()
+        c_dev = torch.zeros(total_c, dtype=torch.complex64, device="cuda")
+        lib.bccb_batch_solve(h, y_dev, iters, None, c_dev, None, True)
+        torch.cuda.synchronize()
+        dev = c_dev.cpu().numpy()
+        kkt_dev = lib.bccb_batch_results(h, len(insts))["kkt"]
+        pageable = np.full(total_c, np.nan, np.complex64)
+        lib.bccb_batch_solve_host(h, y, iters, pageable, True)
+        kkt_host = lib.bccb_batch_results(h, len(insts))["kkt"]
+        y_pin = torch.from_numpy(y).pin_memory()
+        c_pin = torch.full((total_c,), float("nan"), dtype=torch.complex64).pin_memory()
+        lib.bccb_batch_solve_host_ptr(h, y_pin.data_ptr(), iters, c_pin.data_ptr(), True)
+        return dev, pageable, c_pin.numpy().copy(), kkt_dev, kkt_host
+    finally:
+        lib.bccb_destroy(h)
+
+
+@pytest.mark.parametrize("layout", ["packed", "reversed", "gaps"])
+def test_host_entry_point_streams_chunks(lib, layout):
+    """A batch of one shape class with at least 64 instances is solved in chunks whose results
+    are copied back while later chunks run; every layout of c_out (packed, instances in reverse
+    order, gaps between instances, which falls back to one copy) gives the device result."""
+    snaps = [_snap(900 + i, 12, 12, 40, 64, 64, K=2, snr=20.0) for i in range(80)]
+    insts, masks, y, total_c = lib.pack([inst(s, 0.1, True) for s in snaps])
+    L = 64 * 64
+    if layout == "reversed":
+        for i, q in enumerate(insts):
+            q.c_off = (len(insts) - 1 - i) * L
+    elif layout == "gaps":
+        for i, q in enumerate(insts):
+            q.c_off = i * (L + 48)
+        total_c = len(insts) * (L + 48)
+    dev, pageable, pinned, kkt_dev, kkt_host = _solve_dev_and_host(lib, insts, masks, y, total_c, 40)
+    cells = np.zeros(total_c, bool)
+    for q in insts:
+        cells[q.c_off:q.c_off + L] = True
+    np.testing.assert_array_equal(pageable[cells], dev[cells])
+    np.testing.assert_array_equal(pinned[cells], dev[cells])
+    np.testing.assert_array_equal(kkt_host, kkt_dev)
+    # spot parity with the oracle on two instances
+    for i in (0, 79):
+        ref = oracle_run(snaps[i], "fista", 40)
+        q = insts[i]
+        assert_parity(pinned[q.c_off:q.c_off + L], ref, what=f"{layout} instance {i}")
+
+
 # ------------------------------------------------------------------------------------------
 # argument checks (no kernel runs for these)
 # ------------------------------------------------------------------------------------------
