@@ -188,6 +188,10 @@ struct FusedCta {
   uint16_t* poff;   // per active pair: index of its first entry in mtab
   int crank;
   int tid;
+  // every nonzero frequency of this CTA's pairs has q < 2 (the spectrum lives in the first
+  // 2 RP rows, e.g. a 32-row array on a 256-row grid): the split middle stage then forms
+  // and reads only X[0] and X[1] of each 16-point butterfly
+  bool q2 = false;
 
   // ---------------------------------------------------------------------------------------
   // one in-place Stockham stage over all R rows (length L1), radix RS, stride NS; the
@@ -450,6 +454,7 @@ struct FusedCta {
     for (int e = tid; e < NMAX; e += T) tw[e] = twiddle[e * (kTwiddleLen / NMAX)];
     for (int e = tid; e < 256; e += T) tw256[e] = twiddle[((e >> 4) * (e & 15)) * (kTwiddleLen / 256)];
     for (int e = tid; e < 16; e += T) tw16[e] = twiddle[e * (kTwiddleLen / 16)];
+    uint32_t high = 0;
     for (int pl = tid; pl < SH; pl += T) {
       const int p = crank * SH + pl;
       const int k1 = p / L1, col = p % L1;
@@ -459,7 +464,9 @@ struct FusedCta {
         if (mult[f] != 0.f || (bt && (bt[f].x != 0.f || bt[f].y != 0.f))) pm |= 1u << q;
       }
       pmask[pl] = (uint16_t)pm;
+      high |= pm >> 2;
     }
+    q2 = !__syncthreads_or(high != 0u);
     if constexpr (S::SPLIT_MID) {
       // active pair a = (k1 - crank KPO) kc + col; exclusive prefix of the flag counts by
       // one warp (each lane a contiguous chunk), then every thread copies its pairs' entries
@@ -538,6 +545,74 @@ struct FusedCta {
     const int np = KPO * kc;     // active pairs
     const int lane = tid & 31, e = tid & 3;
     const int rounds = (4 * np + T - 1) / T;
+    if (q2) {
+      // Only X[0] and X[1] of each 16-point butterfly, with the arithmetic of the full form
+      // below in the same order (so the nonzero results are the same bits): lane e's inner
+      // 4-point outputs 0 and 1 (the latter times W_16^e), summed over the quad as the outer
+      // 4-point DFT sums them, (s_0 + s_2) + (s_1 + s_3) (xor 2, then xor 1; every lane gets
+      // the same value).  The inverse: lane e's twiddled inverse input W_16^{-e} Y[1] and Y[0]
+      // through the same inverse 4-point DFT, zeros elsewhere.
+      for (int rd = 0; rd < rounds; ++rd) {
+        const int t = rd * T + tid;
+        const bool on = t < 4 * np;
+        const int a = on ? (t >> 2) : 0;
+        const int k1 = crank * KPO + a / kc, col = a % kc;
+        const int pl = (k1 - crank * KPO) * L1 + col;
+        const uint32_t pm = on ? pmask[pl] : 0u;
+        const int pbase = on ? (int)poff[a] : 0;
+        float2 v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int g = e + 4 * i;
+          v[i] = pm ? load(a, k1, col, i) : make_float2(0.f, 0.f);
+          if (g) v[i] = twmul<false>(v[i], tw[g * k1 * (NMAX / L2)]);
+        }
+        float2 x0 = cadd(cadd(v[0], v[2]), cadd(v[1], v[3]));
+        float2 x1 = twmul<false>(cadd(csub(v[0], v[2]), mul_mj<false>(csub(v[1], v[3]))), tw16[e]);
+#pragma unroll
+        for (int m = 2; m >= 1; m >>= 1) {
+          x0.x += __shfl_xor_sync(0xffffffffu, x0.x, m);
+          x0.y += __shfl_xor_sync(0xffffffffu, x0.y, m);
+          x1.x += __shfl_xor_sync(0xffffffffu, x1.x, m);
+          x1.y += __shfl_xor_sync(0xffffffffu, x1.y, m);
+        }
+        float2 y[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const float2 xq = q ? x1 : x0;
+          y[q] = make_float2(0.f, 0.f);
+          if (pm & (1u << q)) {
+            const int idx = pbase + (q ? (int)(pm & 1u) : 0);
+            float mq;
+            float2 b;
+            if (idx < S::MCAP) {
+              const float4 t4 = mtab[idx];
+              mq = t4.x;
+              b = make_float2(t4.y, t4.z);
+            } else {
+              const int f = (k1 + RP * q) * L1 + col;
+              mq = ld_ro_f32(&mult_g[f]);
+              b = bt_g ? ld_ro_f32x2(&bt_g[f]) : make_float2(0.f, 0.f);
+            }
+            y[q] = make_float2(xq.x * mq - b.x, xq.y * mq - b.y);
+          }
+        }
+        v[0] = y[0];
+        v[1] = twmul<true>(y[1], tw16[e]);
+        v[2] = v[3] = make_float2(0.f, 0.f);
+        dft4<true>(v[0], v[1], v[2], v[3]);  // v[i] -> group e + 4 i
+        if (on) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int g = e + 4 * i;
+            float2 o = v[i];
+            if (g) o = twmul<true>(o, tw[g * k1 * (NMAX / L2)]);
+            store(k1, col, i, o);
+          }
+        }
+      }
+      return;
+    }
     for (int rd = 0; rd < rounds; ++rd) {
       const int t = rd * T + tid;
       const bool on = t < 4 * np;
