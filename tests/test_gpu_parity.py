@@ -150,6 +150,29 @@ def test_row256_active_column_counts(lib, algo, M1, L2):
     assert_parity(run["c"][0], ref, what=f"{algo} M1={M1} 256x{L2}")
 
 
+@pytest.mark.parametrize("algo", ["fista", "admm"])
+@pytest.mark.parametrize("M2", [32, 40, 56])
+def test_middle_stage_row_support(lib, algo, M2, tmp_path):
+    """The cross-CTA stage forms only the first two frequencies of its 16-point butterflies
+    on a CTA whose spectrum lies in rows k2 < 32 of the 256-row grid, the full butterfly
+    elsewhere: M2 = 32 puts every CTA on the short form, 40 and 56 mix the two forms in one
+    cluster (k2 < 40: the CTAs with k1 < 8 need q = 2).  Both tiles."""
+    import torch
+
+    s = _snap(800 + M2, 12, M2, (12 * M2) // 4, 256, 256, K=3, snr=15.0, lam_frac=0.08)
+    ref = oracle_run(s, algo, 120, rho=16.0)
+    for tile in (8192, 4096):
+        cache = tmp_path / f"tiles_{tile}.txt"
+        cache.write_text(f"{_gpu_name()} 256 256 {int(algo == 'admm')} {tile}\n")
+        solver = lib.BatchSolver([inst(s, ref["lam"])], algo, 16.0)
+        y = torch.from_numpy(solver.y_host).cuda()
+        lib.bccb_batch_tune(solver.handle, y, 5, str(cache))
+        assert lib.bccb_batch_tile(solver.handle, 256, 256) == tile
+        c = torch.zeros(solver.total_c, dtype=torch.complex64, device="cuda")
+        solver.solve(y, 120, c, check=False)
+        assert_parity(c.cpu().numpy(), ref, what=f"{algo} M2={M2} tile {tile}")
+
+
 # ------------------------------------------------------------------------------------------
 # batched, ragged shapes in one call
 # ------------------------------------------------------------------------------------------
