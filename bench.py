@@ -522,9 +522,18 @@ def run_workload(args):
         s = synth.config_snapshot(1, 0)
         inst = [dict(M1=s.M1, M2=s.M2, L1=s.L1, L2=s.L2, mask=s.mask, y=s.y, lam=0.1, lam_is_frac=True)]
         _, t, _ = _solve_timed(bccb, torch, inst, "fista", 500, reps=5, check=True)
+        per_it_s = t["iterate_ms"] / 500 / 1e3
+        achieved = flops_per_inst_iter(64, 64) / per_it_s / 1e12
+        props = torch.cuda.get_device_properties(0)
+        sm_max = load_peaks().get("sm_max_mhz", 2070.0)
+        sm_peak = FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
         line = {"workload": "single snapshot: 16x16 array, N=64, 64x64 grid, 3 on-grid sources, 20 dB, FISTA 500 "
                             "iterations, lam=0.1||A^H y||_inf", "latency_ms": t,
-                "per_iteration_us": 1e3 * t["iterate_ms"] / 500}
+                "per_iteration_us": 1e6 * per_it_s,
+                # one CTA on one SM: the fraction of that SM's FP32 peak and of the chip's
+                "roofline": {"bound": "alu", "achieved": achieved, "unit": "TFLOP/s", "peak_one_sm": sm_peak,
+                             "frac_one_sm": achieved / sm_peak,
+                             "frac_chip": achieved / (sm_peak * props.multi_processor_count)}}
     elif args.workload == "table1":
         rows = []
         for algo in ("ista", "fista", "admm"):

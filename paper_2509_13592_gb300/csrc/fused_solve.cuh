@@ -192,8 +192,6 @@ struct FusedCta {
   // 2 RP rows, e.g. a 32-row array on a 256-row grid): the split middle stage then forms
   // and reads only X[0] and X[1] of each 16-point butterfly
   bool q2 = false;
-  // likewise with q < 4 (the array reaches k2 < 4 RP, e.g. M2 = L2/4): X[0..3] only
-  bool q4 = false;
 
   // ---------------------------------------------------------------------------------------
   // one in-place Stockham stage over all R rows (length L1), radix RS, stride NS; the
@@ -466,10 +464,9 @@ struct FusedCta {
         if (mult[f] != 0.f || (bt && (bt[f].x != 0.f || bt[f].y != 0.f))) pm |= 1u << q;
       }
       pmask[pl] = (uint16_t)pm;
-      high |= pm;
+      high |= pm >> 2;
     }
-    q2 = !__syncthreads_or((high >> 2) != 0u);
-    q4 = !__syncthreads_or((high >> 4) != 0u);
+    q2 = !__syncthreads_or(high != 0u);
     if constexpr (S::SPLIT_MID) {
       // active pair a = (k1 - crank KPO) kc + col; exclusive prefix of the flag counts by
       // one warp (each lane a contiguous chunk), then every thread copies its pairs' entries
@@ -603,72 +600,6 @@ struct FusedCta {
         v[0] = y[0];
         v[1] = twmul<true>(y[1], tw16[e]);
         v[2] = v[3] = make_float2(0.f, 0.f);
-        dft4<true>(v[0], v[1], v[2], v[3]);  // v[i] -> group e + 4 i
-        if (on) {
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int g = e + 4 * i;
-            float2 o = v[i];
-            if (g) o = twmul<true>(o, tw[g * k1 * (NMAX / L2)]);
-            store(k1, col, i, o);
-          }
-        }
-      }
-      return;
-    }
-    if (q4) {
-      // X[0..3] only, again in the full form's order: lane e's inner 4-point outputs k' (times
-      // W_16^{e k'}) summed over the quad as the outer 4-point DFT's output 0 sums them, so
-      // every lane holds X[k'] for all k' < 4; every lane forms all four Y[k'] and runs the
-      // inverse from them directly (the full form's transpose would hand lane e exactly these).
-      for (int rd = 0; rd < rounds; ++rd) {
-        const int t = rd * T + tid;
-        const bool on = t < 4 * np;
-        const int a = on ? (t >> 2) : 0;
-        const int k1 = crank * KPO + a / kc, col = a % kc;
-        const int pl = (k1 - crank * KPO) * L1 + col;
-        const uint32_t pm = on ? pmask[pl] : 0u;
-        const int pbase = on ? (int)poff[a] : 0;
-        float2 v[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int g = e + 4 * i;
-          v[i] = pm ? load(a, k1, col, i) : make_float2(0.f, 0.f);
-          if (g) v[i] = twmul<false>(v[i], tw[g * k1 * (NMAX / L2)]);
-        }
-        dft4<false>(v[0], v[1], v[2], v[3]);
-#pragma unroll
-        for (int i = 1; i < 4; ++i) v[i] = twmul<false>(v[i], tw16[e * i]);
-#pragma unroll
-        for (int m = 2; m >= 1; m >>= 1) {
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            v[k].x += __shfl_xor_sync(0xffffffffu, v[k].x, m);
-            v[k].y += __shfl_xor_sync(0xffffffffu, v[k].y, m);
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          if (pm & (1u << q)) {
-            const int idx = pbase + __popc(pm & ((1u << q) - 1u));
-            float mq;
-            float2 b;
-            if (idx < S::MCAP) {
-              const float4 t4 = mtab[idx];
-              mq = t4.x;
-              b = make_float2(t4.y, t4.z);
-            } else {
-              const int f = (k1 + RP * q) * L1 + col;
-              mq = ld_ro_f32(&mult_g[f]);
-              b = bt_g ? ld_ro_f32x2(&bt_g[f]) : make_float2(0.f, 0.f);
-            }
-            v[q] = make_float2(v[q].x * mq - b.x, v[q].y * mq - b.y);
-          } else {
-            v[q] = make_float2(0.f, 0.f);
-          }
-        }
-#pragma unroll
-        for (int i = 1; i < 4; ++i) v[i] = twmul<true>(v[i], tw16[e * i]);
         dft4<true>(v[0], v[1], v[2], v[3]);  // v[i] -> group e + 4 i
         if (on) {
 #pragma unroll

@@ -153,12 +153,11 @@ def test_row256_active_column_counts(lib, algo, M1, L2):
 @pytest.mark.parametrize("algo", ["fista", "admm"])
 @pytest.mark.parametrize("M2", [32, 40, 56, 72])
 def test_middle_stage_row_support(lib, algo, M2, tmp_path):
-    """The cross-CTA stage forms only the first two (four) frequencies of its 16-point
-    butterflies on a CTA whose spectrum lies in rows k2 < 32 (64) of the 256-row grid, the
-    full butterfly elsewhere: M2 = 32 puts every CTA on the two-frequency form, 40 mixes the
-    two- and four-frequency forms in one cluster (k2 < 40: the CTAs with k1 < 8 need q = 2),
-    56 puts every CTA on the four-frequency form and 72 mixes it with the full form.  Both
-    tiles."""
+    """The cross-CTA stage forms only the first two frequencies of its 16-point butterflies
+    on a CTA whose spectrum lies in rows k2 < 32 of the 256-row grid, the full butterfly
+    elsewhere: M2 = 32 puts every CTA on the short form, 40 mixes the two forms in one cluster
+    (k2 < 40: the CTAs with k1 < 8 need q = 2), 56 and 72 put every CTA on the full form.
+    Both tiles."""
     import torch
 
     s = _snap(800 + M2, 12, M2, (12 * M2) // 4, 256, 256, K=3, snr=15.0, lam_frac=0.08)
