@@ -150,6 +150,46 @@ def cpu_oracle_sample(n_inst, iters, first=0):
     return n_inst * iters / dt, dt
 
 
+def cpu_fft_sample(n_inst, iters, first=0):
+    """The paper's fast method (Section III-B) on the host cores, as timing context beside the
+    dense oracle: FISTA on a batch of snapshots whose Gram products are IFFT2(Omega . FFT2(z))
+    (eq:Rc) in FP64 with scipy.fft on every core; Omega is the FFT2 of the Gram's first column
+    (eq:lambda), and A, b, lam come from the oracle (setup, not timed).  Returns instance-
+    iterations per second of the iterations, the seconds they took and the last iterates
+    (n_inst, L2, L1)."""
+    import numpy as np
+    import scipy.fft
+
+    import oracle
+
+    snaps = make_batch(n_inst, first)
+    L1, L2 = WORKLOAD["L1"], WORKLOAD["L2"]
+    omega = np.empty((n_inst, L2, L1))
+    b = np.empty((n_inst, L2, L1), np.complex128)
+    mu = np.empty((n_inst, 1, 1))
+    kappa = np.empty((n_inst, 1, 1))
+    for i, s in enumerate(snaps):
+        A = oracle.dictionary(s.mask, s.M1, s.M2, L1, L2)
+        omega[i] = scipy.fft.fft2(oracle.gram_first_column(A).reshape(L2, L1)).real
+        b[i] = oracle.adjoint_measurements(A, s.y).reshape(L2, L1)
+        mu[i] = 1.0 / omega[i].max()
+        kappa[i] = mu[i] * WORKLOAD["lam_frac"] * np.abs(b[i]).max()
+    beta = oracle.fista_momentum(iters)
+    workers = os.cpu_count()
+    c_prev = np.zeros_like(b)
+    z = c_prev.copy()
+    t0 = time.perf_counter()
+    for t in range(iters):
+        g = scipy.fft.ifft2(omega * scipy.fft.fft2(z, workers=workers), workers=workers)
+        u = z - mu * g + mu * b
+        mag = np.abs(u)
+        c = u * (np.maximum(mag - kappa, 0.0) / np.where(mag > 0.0, mag, 1.0))
+        z = c + beta[t] * (c - c_prev)
+        c_prev = c
+    dt = time.perf_counter() - t0
+    return n_inst * iters / dt, dt, c_prev
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -352,6 +392,12 @@ def run_gpu(args, rank, world, local_rank):
             cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                    "sample": f"{n_cpu} snapshots x {it_cpu} FISTA iterations of the same workload, dense FP64 "
                              f"oracle with setup ({dt:.1f} s)"}
+            n_fft, it_fft = 8, 200
+            v_fft, dt_fft, _ = cpu_fft_sample(n_fft, it_fft, first=10**6)
+            cpu["fft_method"] = {"value": v_fft, "unit": UNIT, "cores": os.cpu_count(),
+                                 "kind": "the paper's FFT method on the host (FP64, scipy.fft on every core)",
+                                 "sample": f"{n_fft} snapshots x {it_fft} FISTA iterations of the same workload, "
+                                           f"iterations only ({dt_fft:.1f} s)"}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
