@@ -553,6 +553,7 @@ struct FusedCta {
       // the same value).  The inverse: lane e's twiddled inverse input W_16^{-e} Y[1] and Y[0]
       // through the same inverse 4-point DFT, zeros elsewhere.
       for (int rd = 0; rd < rounds; ++rd) {
+        if (rd * T + (tid & ~31) >= 4 * np) break;  // the whole warp is past the active pairs
         const int t = rd * T + tid;
         const bool on = t < 4 * np;
         const int a = on ? (t >> 2) : 0;
@@ -614,6 +615,7 @@ struct FusedCta {
       return;
     }
     for (int rd = 0; rd < rounds; ++rd) {
+      if (rd * T + (tid & ~31) >= 4 * np) break;  // the whole warp is past the active pairs
       const int t = rd * T + tid;
       const bool on = t < 4 * np;
       const int a = on ? (t >> 2) : 0;
