@@ -54,13 +54,15 @@ __global__ void fft64_rows_kernel(const InstDesc* __restrict__ desc, const int* 
 int cols_per_block(int max_L2) { return max_L2 <= 512 ? 8 : 4096 / max_L2; }
 
 // In-place DFT of every column (length L2) of every instance's grid (of the instances sel
-// lists, when sel is given), cpb at a time.
+// lists, when sel is given), cpb at a time; with lim given, only columns < lim[i].kcols.
 __global__ void fft64_cols_kernel(const InstDesc* __restrict__ desc, const int* __restrict__ sel, double2* base,
-                                  int inv, const double2* __restrict__ tw, int cpb) {
-  const InstDesc d = desc[sel ? sel[blockIdx.x] : blockIdx.x];
+                                  int inv, const double2* __restrict__ tw, int cpb, const FusedInst* __restrict__ lim) {
+  const int i = sel ? sel[blockIdx.x] : blockIdx.x;
+  const InstDesc d = desc[i];
+  const int ncols = lim ? min(d.L1, lim[i].kcols) : d.L1;
   const int c0 = blockIdx.y * cpb;
-  if (c0 >= d.L1) return;
-  const int cnt = min(cpb, d.L1 - c0);
+  if (c0 >= ncols) return;
+  const int cnt = min(cpb, ncols - c0);
   extern __shared__ double2 sm64[];
   double2* x = sm64;
   double2* y = sm64 + d.L2 * cnt;
@@ -316,18 +318,28 @@ dim3 grid_cells(const bccb_solver* s) {
   return dim3((unsigned)s->n, (unsigned)(blocks < 64 ? blocks : 64));
 }
 
-// FFT2 of every instance's grid, or of the `count` instances listed in sel; rows > 0 says that
-// every row from `rows` on is zero in each grid (the rows pass then launches only the others).
-cudaError_t fft2_64(bccb_solver* s, double2* grid, int inv, int rows = 0, const int* sel = nullptr, int count = 0) {
-  s->launches += 2;
+void fft64_rows(bccb_solver* s, double2* grid, int inv, int rows, const int* sel, int count) {
   const int nb = sel ? count : s->n;
   const int ry = rows > 0 ? std::min(rows, s->max_L2) : s->max_L2;
   const size_t smr = (size_t)2 * s->max_L1 * sizeof(double2);
   fft64_rows_kernel<<<dim3(nb, ry), 128, smr, s->stream>>>(s->d_desc, sel, grid, inv, s->d_tw64);
+  s->launches += 1;
+}
+
+void fft64_cols(bccb_solver* s, double2* grid, int inv, const int* sel, int count, const FusedInst* lim) {
+  const int nb = sel ? count : s->n;
   const int cpb = cols_per_block(s->max_L2);
   const size_t smc = (size_t)2 * s->max_L2 * cpb * sizeof(double2);
   fft64_cols_kernel<<<dim3(nb, (s->max_L1 + cpb - 1) / cpb), 128, smc, s->stream>>>(s->d_desc, sel, grid, inv,
-                                                                                     s->d_tw64, cpb);
+                                                                                     s->d_tw64, cpb, lim);
+  s->launches += 1;
+}
+
+// FFT2 of every instance's grid, or of the `count` instances listed in sel; rows > 0 says that
+// every row from `rows` on is zero in each grid (the rows pass then launches only the others).
+cudaError_t fft2_64(bccb_solver* s, double2* grid, int inv, int rows = 0, const int* sel = nullptr, int count = 0) {
+  fft64_rows(s, grid, inv, rows, sel, count);
+  fft64_cols(s, grid, inv, sel, count, nullptr);
   return cudaGetLastError();
 }
 
@@ -708,10 +720,16 @@ cudaError_t run_check_t(bccb_solver* s, const V* y_dev, const V* c_dev) {
   const dim3 gc = grid_cells(s);
   load_solution_kernel<V><<<gc, kThreads, 0, s->stream>>>(s->d_desc, c_dev, s->d_w64);
   s->launches += 4;  // load_solution, data_residual, mul_lambda, kkt_final
-  cudaError_t err;
-  if ((err = fft2_64(s, s->d_w64, 0)) != cudaSuccess) return err;
+  // Lambda vanishes on the Fourier columns from kcols on (as q does), and the data residual
+  // reads FFT2(c) only at the element positions, where Lambda > 0: the forward column pass
+  // transforms only the columns below kcols, and the product Lambda . FFT2(c) zeroes the rest
+  // (they hold finite row-pass values).  The inverse is the plain FFT2, whose row pass skips
+  // the rows that product leaves at zero.
+  fft64_rows(s, s->d_w64, 0, 0, nullptr, 0);
+  fft64_cols(s, s->d_w64, 0, nullptr, 0, s->d_fused);
   data_residual_kernel<V><<<s->n, kThreads, 0, s->stream>>>(s->d_desc, s->d_mask_idx, y_dev, s->d_w64, s->d_red);
   mul_lambda_kernel<<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_lam64, s->d_w64);
+  cudaError_t err;
   if ((err = fft2_64(s, s->d_w64, 1)) != cudaSuccess) return err;
   kkt_final_kernel<V><<<s->n, kThreads, 0, s->stream>>>(s->d_desc, s->d_b64, s->d_w64, c_dev, s->d_par, s->d_red,
                                                          s->d_kkt, s->d_obj);
