@@ -43,7 +43,8 @@ def _worker(rank, world, port, out):
 
 def test_two_gloo_ranks_shard_and_take_the_max():
     port = _free_port()
-    with mp.Manager() as m:
+    # spawn, not fork: earlier tests may have left threads (BLAS, FFT workers) in this process
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
         res = dict(out)
