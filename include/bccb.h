@@ -80,7 +80,9 @@ typedef struct {
 
 /* Create a solver for a batch of n independent instances that share one algorithm
  * (and, for ADMM, one rho > 0; eq:admm).  Copies the masks and instance table to
- * the device; allocates all internal buffers.  Does not launch the solve.
+ * the device; allocates all internal buffers.  Does not launch the solve.  Instances
+ * with the same M1, M2, L1, L2 and mask (a fixed array observing many snapshots)
+ * share one Lambda transform in every setup; results are as if each had its own.
  * Errors: INVALID_ARG (n < 1, null pointers, empty mask, bad algo/rho,
  * reserved != 0), UNSUPPORTED (grid size), CUDA. */
 int bccb_batch_create(bccb_solver_t* out, const bccb_inst_t* insts, int n, const uint8_t* masks_host,
