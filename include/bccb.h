@@ -61,7 +61,7 @@ enum {
   BCCB_ERR_INVALID_ARG = 1, /* null pointer, bad size, empty mask, rho <= 0, ... */
   BCCB_ERR_UNSUPPORTED = 2, /* grid size outside the supported set */
   BCCB_ERR_CUDA = 3,        /* a CUDA call failed; see bccb_last_error() */
-  BCCB_ERR_KKT = 4,         /* reserved: result returned but the KKT check failed */
+  BCCB_ERR_KKT = 4,         /* result returned, but its FP64 KKT check failed (bccb_batch_solve) */
   BCCB_ERR_TIMEOUT = 5      /* reserved: a bounded device wait expired */
 };
 
@@ -121,10 +121,32 @@ int bccb_batch_create_gamma(bccb_solver_t* out, const bccb_inst_t* insts, int n,
  * y_dev: packed complex64 measurements (device).  c0_dev: nullable warm start
  * (complex64, same packing as c_out_dev; ADMM: z^(0)).  c_out_dev: packed complex64
  * results: c^(T) for ISTA/FISTA, z^(T) for ADMM.  aux_out_dev: nullable; ADMM
- * writes c^(T) there.  Asynchronous.  Errors: INVALID_ARG (null y/c_out,
- * iters < 1), CUDA. */
+ * writes c^(T) there.  Asynchronous unless status_out is given.
+ * status_out: nullable host array of n ints.  When given, the FP64 check runs whatever
+ * `check` says, the call synchronises the stream and writes, per instance, BCCB_OK or
+ * BCCB_ERR_KKT: the relative KKT residual of the LASSO optimality conditions
+ * (Section II-A; see bccb_batch_results) exceeds the solver's tolerance
+ * (bccb_set_kkt_tol, default 1e-2), or is not a number.  The call then returns
+ * BCCB_ERR_KKT if any instance failed; every result is still written.  status_out is
+ * refused (INVALID_ARG) inside a stream capture, which cannot synchronise.
+ * Errors: INVALID_ARG (null y/c_out, iters < 1), KKT, CUDA. */
 int bccb_batch_solve(bccb_solver_t s, const void* y_dev, int iters, const void* c0_dev, void* c_out_dev,
-                     void* aux_out_dev, int check);
+                     void* aux_out_dev, int check, int* status_out);
+
+/* Tolerance on the relative KKT residual behind status BCCB_ERR_KKT (tol > 0). */
+int bccb_set_kkt_tol(bccb_solver_t s, double tol);
+
+/* Per-instance status of the last solve that ran the FP64 check (bccb_batch_solve with
+ * check or status_out, bccb_unrolled_fwd with check), as bccb_batch_solve's status_out:
+ * BCCB_OK or BCCB_ERR_KKT per instance in the host array status_out[0..n-1]; returns
+ * BCCB_ERR_KKT if any failed, INVALID_ARG if the last solve ran no check.  Synchronises. */
+int bccb_batch_status(bccb_solver_t s, int* status_out);
+
+/* Step size mu = 1/sigma_max(A)^2 of each instance (eq:ista), written to the host array
+ * mu[0..n-1]: 1/max Lambda for half-wavelength spacing (eq:lambda), the power-iteration
+ * value for gamma != 1/2.  mu depends on the mask alone; if no solve has been queued yet,
+ * the call runs the setup on the mask (with y = 0) first.  Synchronises. */
+int bccb_mu(bccb_solver_t s, double* mu);
 
 /* bccb_batch_solve with HOST buffers: copies y to the device, solves, copies c
  * back; synchronises.  y_host / c_out_host use the same packing as above.  A batch
@@ -148,9 +170,10 @@ int bccb_batch_results(bccb_solver_t s, double* kkt, double* obj, double* lam, d
  * [p2][p1] and include 1/(L1 L2).  Asynchronous. */
 int bccb_batch_get(bccb_solver_t s, int what, void* dst_dev);
 
-/* Single-instance convenience: a batch of one (c_off = y_off = 0). */
+/* Single-instance convenience: a batch of one (c_off = y_off = 0) with the arithmetic
+ * prec (BCCB_F32 or BCCB_F64, as bccb_batch_create2). */
 int bccb_create(bccb_solver_t* out, int M1, int M2, const uint8_t* mask_host, int L1, int L2, int algo,
-                double rho, void* cuda_stream);
+                double rho, int prec, void* cuda_stream);
 /* Solve one instance with LASSO weight lam (absolute, or a fraction of
  * ||A^H y||_inf if lam_is_frac).  kkt_out / obj_out nullable; when either is
  * given the FP64 check runs and the call synchronises. */
@@ -180,7 +203,8 @@ int bccb_batch_tile(bccb_solver_t s, int L1, int L2, int* tile);
  *     u_k = z_k - a_k mu (G z_k - b),  c_k = S_{t_k mu lam}(u_k),  z_{k+1} = c_k + beta_k (c_k - c_{k-1})
  * with z_0 = c_{-1} = 0, FISTA's beta_k, and per-layer multipliers a_k = scale_dev[k],
  * t_k = thresh_dev[k] (device float arrays; a = t = 1 is plain FISTA with `layers`
- * iterations).  bccb_unrolled_fwd runs the setup and the layers, writes c_{K-1} to
+ * iterations).  batch is the number of snapshots and must equal the solver's instance
+ * count (INVALID_ARG otherwise).  bccb_unrolled_fwd runs the setup and the layers, writes c_{K-1} to
  * c_out_dev, and, if saved_dev is not NULL, stores each layer's input z_k and
  * mu (G z_k - b) there (layers * 2 * (packed solution length) complex64 values) for
  * the backward pass; check != 0 runs the FP64 KKT check on c_{K-1}.
@@ -189,9 +213,9 @@ int bccb_batch_tile(bccb_solver_t s, int L1, int L2, int* tile);
  * to the device float64 arrays grad_scale_dev / grad_thresh_dev (length layers).  It
  * needs the same solver, layers, multipliers and saved buffer as the forward call.
  * Square grids (L1 = L2, up to 256) only; BCCB_ERR_UNSUPPORTED otherwise. */
-int bccb_unrolled_fwd(bccb_solver_t s, const void* y_dev, int layers, const float* scale_dev,
+int bccb_unrolled_fwd(bccb_solver_t s, const void* y_dev, int batch, int layers, const float* scale_dev,
                       const float* thresh_dev, void* c_out_dev, void* saved_dev, int check);
-int bccb_unrolled_bwd(bccb_solver_t s, int layers, const float* scale_dev, const float* thresh_dev,
+int bccb_unrolled_bwd(bccb_solver_t s, int batch, int layers, const float* scale_dev, const float* thresh_dev,
                       const void* saved_dev, const void* grad_c_dev, double* grad_scale_dev, double* grad_thresh_dev);
 
 /* Phase timing of bccb_batch_solve, for profiling.  bccb_set_timing(s, 1) makes
@@ -259,7 +283,7 @@ int bccb_destroy(bccb_solver_t s);
  * allocation can bring).  The paper has no counterpart; this is a deployment
  * convenience over the same kernels as bccb_solve.
  *
- * All working memory (about 3.4 MB) is one fixed array compiled into the
+ * All working memory (about 3.9 MB) is one fixed array compiled into the
  * library, which every GPU that loads the library holds until the process
  * exits.  The first call on each device looks that array up and uploads the
  * twiddle tables (make that first call before any stream capture); later calls
@@ -269,7 +293,12 @@ int bccb_destroy(bccb_solver_t s);
  * nothing left by an earlier call leaks into a result.
  *
  * Arguments as for bccb_create + bccb_solve, except that the mask is a DEVICE
- * pointer (uint8, M1*M2) and there is no KKT check.  Limits: L1, L2 powers of
+ * pointer (uint8, M1*M2) and there is no KKT check.  The mask cannot be inspected
+ * on the host, so an all-zero mask is not refused: with no element kept, A has no
+ * rows and c_out receives c = 0, the minimiser of the data-free problem (mu is
+ * taken as 0 instead of 1/max Lambda = 1/0).  The device address of the array is
+ * looked up on every call, so the set-up runs again after cudaDeviceReset.
+ * Limits: L1, L2 powers of
  * two in [16, 256] (L1*L2 <= 65536), M1*M2 <= 16384, 1 <= iters <= 8192; larger
  * sizes return BCCB_ERR_UNSUPPORTED before any work is queued.  Asynchronous on
  * cuda_stream; y_dev and c_out_dev as for bccb_solve (c_out receives c^(T), or

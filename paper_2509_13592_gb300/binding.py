@@ -49,11 +49,14 @@ def _load():
     lib.bccb_batch_create.argtypes = [P(vp), P(bccb_inst_t), i32, vp, i32, dbl, vp]
     lib.bccb_batch_create2.argtypes = [P(vp), P(bccb_inst_t), i32, vp, i32, dbl, i32, vp]
     lib.bccb_batch_create_gamma.argtypes = [P(vp), P(bccb_inst_t), i32, vp, i32, dbl, i32, dbl, dbl, vp]
-    lib.bccb_batch_solve.argtypes = [vp, vp, i32, vp, vp, vp, i32]
+    lib.bccb_batch_solve.argtypes = [vp, vp, i32, vp, vp, vp, i32, vp]
+    lib.bccb_set_kkt_tol.argtypes = [vp, dbl]
+    lib.bccb_mu.argtypes = [vp, vp]
+    lib.bccb_batch_status.argtypes = [vp, vp]
     lib.bccb_batch_solve_host.argtypes = [vp, vp, i32, vp, i32]
     lib.bccb_batch_results.argtypes = [vp, vp, vp, vp, vp]
     lib.bccb_batch_get.argtypes = [vp, i32, vp]
-    lib.bccb_create.argtypes = [P(vp), i32, i32, vp, i32, i32, i32, dbl, vp]
+    lib.bccb_create.argtypes = [P(vp), i32, i32, vp, i32, i32, i32, dbl, i32, vp]
     lib.bccb_solve.argtypes = [vp, vp, dbl, i32, i32, vp, vp, vp, P(dbl), P(dbl)]
     lib.bccb_set_timing.argtypes = [vp, i32]
     lib.bccb_last_timing.argtypes = [vp, P(ctypes.c_float), P(ctypes.c_float), P(ctypes.c_float),
@@ -62,8 +65,8 @@ def _load():
     lib.bccb_batch_replay.argtypes = [vp]
     lib.bccb_batch_tune.argtypes = [vp, vp, i32, ctypes.c_char_p]
     lib.bccb_batch_tile.argtypes = [vp, i32, i32, P(i32)]
-    lib.bccb_unrolled_fwd.argtypes = [vp, vp, i32, vp, vp, vp, vp, i32]
-    lib.bccb_unrolled_bwd.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp]
+    lib.bccb_unrolled_fwd.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, i32]
+    lib.bccb_unrolled_bwd.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp]
     lib.bccb_batch_peaks.argtypes = [vp, vp, i32, dbl, vp, vp, vp, vp, vp]
     lib.bccb_batch_set_method.argtypes = [vp, i32]
     lib.bccb_batch_size.argtypes = [vp, P(i32)]
@@ -77,7 +80,7 @@ def _load():
                  "bccb_batch_get", "bccb_create", "bccb_solve", "bccb_batch_size", "bccb_instance_shape",
                  "bccb_destroy", "bccb_set_timing", "bccb_last_timing", "bccb_batch_capture", "bccb_batch_replay",
                  "bccb_batch_tune", "bccb_batch_tile", "bccb_unrolled_fwd", "bccb_unrolled_bwd", "bccb_batch_peaks",
-                 "bccb_batch_set_method", "bccb_batch_create_gamma"):
+                 "bccb_batch_set_method", "bccb_batch_create_gamma", "bccb_set_kkt_tol", "bccb_mu", "bccb_batch_status"):
         getattr(lib, name).restype = i32
     return lib
 
@@ -128,9 +131,40 @@ def bccb_batch_create(insts: Sequence[bccb_inst_t], masks_host: np.ndarray, algo
     return h.value
 
 
-def bccb_batch_solve(h: int, y_dev, iters: int, c0_dev, c_out_dev, aux_out_dev=None, check: bool = True) -> None:
-    _raise(_lib.bccb_batch_solve(h, _ptr(y_dev), int(iters), _ptr(c0_dev), _ptr(c_out_dev), _ptr(aux_out_dev),
-                                 1 if check else 0), h)
+def bccb_batch_solve(h: int, y_dev, iters: int, c0_dev, c_out_dev, aux_out_dev=None, check: bool = True,
+                     status_out: Optional[np.ndarray] = None) -> int:
+    """With ``status_out`` (int32 numpy array of n entries) the per-instance KKT status is
+    written there and the call returns BCCB_ERR_KKT instead of raising when only that failed."""
+    sp = None
+    if status_out is not None:
+        if not (isinstance(status_out, np.ndarray) and status_out.dtype == np.int32 and status_out.flags.c_contiguous):
+            raise ValueError("status_out must be a C-contiguous int32 numpy array")
+        sp = status_out.ctypes.data_as(ctypes.c_void_p)
+    st = _lib.bccb_batch_solve(h, _ptr(y_dev), int(iters), _ptr(c0_dev), _ptr(c_out_dev), _ptr(aux_out_dev),
+                               1 if check else 0, sp)
+    if st == ERR_KKT and status_out is not None:
+        return st
+    _raise(st, h)
+    return st
+
+
+def bccb_set_kkt_tol(h: int, tol: float) -> None:
+    _raise(_lib.bccb_set_kkt_tol(h, float(tol)), h)
+
+
+def bccb_batch_status(h: int, n: int) -> np.ndarray:
+    """Per-instance status (OK or ERR_KKT) of the last checked solve, as int32 (n,)."""
+    st = np.zeros(n, np.int32)
+    r = _lib.bccb_batch_status(h, st.ctypes.data_as(ctypes.c_void_p))
+    if r != ERR_KKT:
+        _raise(r, h)
+    return st
+
+
+def bccb_mu(h: int, n: int) -> np.ndarray:
+    mu = np.zeros(n)
+    _raise(_lib.bccb_mu(h, mu.ctypes.data_as(ctypes.c_void_p)), h)
+    return mu
 
 
 def bccb_batch_solve_host(h: int, y_host: np.ndarray, iters: int, c_out_host: np.ndarray, check: bool = True) -> None:
@@ -154,13 +188,13 @@ def bccb_batch_get(h: int, what: int, dst_dev) -> None:
 
 
 def bccb_create(M1: int, M2: int, mask_host: np.ndarray, L1: int, L2: int, algo: int, rho: float = 1.0,
-                stream=None) -> int:
+                stream=None, prec: int = F32) -> int:
     m = np.ascontiguousarray(mask_host, dtype=np.uint8).reshape(-1)
     if m.size != M1 * M2:
         raise ValueError("mask must have M1*M2 entries")
     h = ctypes.c_void_p()
     _raise(_lib.bccb_create(ctypes.byref(h), int(M1), int(M2), m.ctypes.data_as(ctypes.c_void_p), int(L1),
-                            int(L2), int(algo), float(rho), _stream(stream)), None)
+                            int(L2), int(algo), float(rho), int(prec), _stream(stream)), None)
     return h.value
 
 
@@ -194,15 +228,15 @@ def bccb_batch_tile(h: int, L1: int, L2: int) -> int:
     return t.value
 
 
-def bccb_unrolled_fwd(h: int, y_dev, layers: int, scale_dev, thresh_dev, c_out_dev, saved_dev=None,
+def bccb_unrolled_fwd(h: int, y_dev, batch: int, layers: int, scale_dev, thresh_dev, c_out_dev, saved_dev=None,
                       check: bool = False) -> None:
-    _raise(_lib.bccb_unrolled_fwd(h, _ptr(y_dev), int(layers), _ptr(scale_dev), _ptr(thresh_dev), _ptr(c_out_dev),
-                                  _ptr(saved_dev), 1 if check else 0), h)
+    _raise(_lib.bccb_unrolled_fwd(h, _ptr(y_dev), int(batch), int(layers), _ptr(scale_dev), _ptr(thresh_dev),
+                                  _ptr(c_out_dev), _ptr(saved_dev), 1 if check else 0), h)
 
 
-def bccb_unrolled_bwd(h: int, layers: int, scale_dev, thresh_dev, saved_dev, grad_c_dev, grad_scale_dev,
-                      grad_thresh_dev) -> None:
-    _raise(_lib.bccb_unrolled_bwd(h, int(layers), _ptr(scale_dev), _ptr(thresh_dev), _ptr(saved_dev),
+def bccb_unrolled_bwd(h: int, batch: int, layers: int, scale_dev, thresh_dev, saved_dev, grad_c_dev,
+                      grad_scale_dev, grad_thresh_dev) -> None:
+    _raise(_lib.bccb_unrolled_bwd(h, int(batch), int(layers), _ptr(scale_dev), _ptr(thresh_dev), _ptr(saved_dev),
                                   _ptr(grad_c_dev), _ptr(grad_scale_dev), _ptr(grad_thresh_dev)), h)
 
 
@@ -282,9 +316,12 @@ class BatchSolver:
         self.offsets = [(q.c_off, q.L1, q.L2) for q in self.insts]
         self.handle = bccb_batch_create(self.insts, self.masks, self.algo, rho, stream, self.prec, gamma)
 
-    def solve(self, y_dev, iters, c_out, c0=None, aux_out=None, check=True):
-        bccb_batch_solve(self.handle, y_dev, iters, c0, c_out, aux_out, check)
+    def solve(self, y_dev, iters, c_out, c0=None, aux_out=None, check=True, status_out=None):
+        bccb_batch_solve(self.handle, y_dev, iters, c0, c_out, aux_out, check, status_out)
         return c_out
+
+    def mu(self):
+        return bccb_mu(self.handle, self.n)
 
     def solve_host(self, y_host, iters, c_out_host, check=True):
         bccb_batch_solve_host(self.handle, y_host, iters, c_out_host, check)

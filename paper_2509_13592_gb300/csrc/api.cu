@@ -98,7 +98,8 @@ void release(bccb_solver* s) {
                   s->d_cterm,  s->d_par,      s->d_fused,   s->d_ids,     s->d_beta,    s->d_beta64,
                   s->d_kkt,    s->d_obj,      s->d_red,     s->d_tw32,    s->d_tw64,    s->d_y_stage,
                   s->d_c_stage, s->d_mult64,  s->d_bt64,    s->d_mp_work, s->d_mp_s0,   s->d_mp_s1,
-                  s->d_cint,   s->d_c0int,    s->d_toep_h,  s->d_toep_fb, s->d_lam_sel, s->d_lam_src};
+                  s->d_cint,   s->d_c0int,    s->d_toep_h,  s->d_toep_fb, s->d_lam_sel, s->d_lam_src,
+                  s->d_lo};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -317,8 +318,15 @@ int create_impl(bccb_solver_t* out, const bccb_inst_t* insts, int n, const uint8
     CREATE_CUDA(bccb::prepare_multipass(s));
   }
   CREATE_CUDA(bccb::fill_twiddles(s));
+  bool any_fused = false;
   for (auto& c : s->classes)
-    if (!c.multipass) CREATE_CUDA(c.entry.prepare());
+    if (!c.multipass) {
+      CREATE_CUDA(c.entry.prepare());
+      any_fused = true;
+    }
+  // the fused ISTA/FISTA kernel keeps the low-order parts of its state here (8 bytes per cell;
+  // only cells where the state is nonzero are ever read or written, so no initialisation)
+  if (any_fused && algo != BCCB_ADMM) CREATE_CUDA(dalloc(&s->d_lo, s->total_c));
   if (s->classes.size() > 1) {
     CREATE_CUDA(cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming));
     for (size_t k = 0; k < s->classes.size(); ++k) {
@@ -418,6 +426,13 @@ int solve_impl(bccb_solver_t s, const void* y_dev, int iters, const void* c0_dev
   } else {
     BCCB_CUDA(s, bccb::run_setup(s, y));
   }
+  {
+    // mu depends on the mask alone: once a setup has been queued outside a capture,
+    // bccb_mu can read it after a synchronisation
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    BCCB_CUDA(s, cudaStreamIsCapturing(s->stream, &cs));
+    if (cs == cudaStreamCaptureStatusNone) s->mu_ready = 1;
+  }
   if (s->timing) BCCB_CUDA(s, record_timing(s, 1));
   FusedArgs a{};
   a.insts = s->d_fused;
@@ -428,6 +443,7 @@ int solve_impl(bccb_solver_t s, const void* y_dev, int iters, const void* c0_dev
   a.c0 = reinterpret_cast<const float2*>(k_c0);
   a.c_out = reinterpret_cast<float2*>(k_out);
   a.aux_out = (s->algo == BCCB_ADMM) ? reinterpret_cast<float2*>(aux_out_dev) : nullptr;
+  a.lo = s->d_lo;
   a.iters = iters;
   a.pad_ = 0;
   if (s->method == BCCB_DENSE) {
@@ -561,8 +577,64 @@ int bccb_batch_create_gamma(bccb_solver_t* out, const bccb_inst_t* insts, int n,
 }
 
 int bccb_batch_solve(bccb_solver_t s, const void* y_dev, int iters, const void* c0_dev, void* c_out_dev,
-                     void* aux_out_dev, int check) {
-  return solve_impl(s, y_dev, iters, c0_dev, c_out_dev, aux_out_dev, check, nullptr);
+                     void* aux_out_dev, int check, int* status_out) {
+  if (s && status_out) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    BCCB_CUDA(s, cudaSetDevice(s->device));
+    BCCB_CUDA(s, cudaStreamIsCapturing(s->stream, &cs));
+    if (cs != cudaStreamCaptureStatusNone)
+      return fail(s, BCCB_ERR_INVALID_ARG, "status_out needs a synchronisation, which a stream capture forbids");
+  }
+  const int st = solve_impl(s, y_dev, iters, c0_dev, c_out_dev, aux_out_dev, check || status_out, nullptr);
+  if (st != BCCB_OK || !status_out) return st;
+  return bccb_batch_status(s, status_out);
+}
+
+int bccb_batch_status(bccb_solver_t s, int* status_out) {
+  if (!s) return fail(nullptr, BCCB_ERR_INVALID_ARG, "solver is NULL");
+  if (!status_out) return fail(s, BCCB_ERR_INVALID_ARG, "status_out is NULL");
+  if (!s->last_checked) return fail(s, BCCB_ERR_INVALID_ARG, "the last solve ran without the FP64 check");
+  BCCB_CUDA(s, cudaSetDevice(s->device));
+  std::vector<double> kkt(s->n);
+  BCCB_CUDA(s, cudaStreamSynchronize(s->stream));
+  BCCB_CUDA(s, cudaMemcpy(kkt.data(), s->d_kkt, s->n * sizeof(double), cudaMemcpyDeviceToHost));
+  int failed = 0;
+  for (int i = 0; i < s->n; ++i) {
+    // a NaN residual fails too
+    status_out[i] = kkt[i] <= s->kkt_tol ? BCCB_OK : BCCB_ERR_KKT;
+    failed += status_out[i] != BCCB_OK;
+  }
+  if (failed)
+    return fail(s, BCCB_ERR_KKT, std::to_string(failed) + " of " + std::to_string(s->n) +
+                                     " instances above the KKT tolerance");
+  return BCCB_OK;
+}
+
+int bccb_set_kkt_tol(bccb_solver_t s, double tol) {
+  if (!s) return fail(nullptr, BCCB_ERR_INVALID_ARG, "solver is NULL");
+  if (!(tol > 0.0)) return fail(s, BCCB_ERR_INVALID_ARG, "tol must be > 0");
+  s->kkt_tol = tol;
+  return BCCB_OK;
+}
+
+int bccb_mu(bccb_solver_t s, double* mu) {
+  if (!s) return fail(nullptr, BCCB_ERR_INVALID_ARG, "solver is NULL");
+  if (!mu) return fail(s, BCCB_ERR_INVALID_ARG, "mu is NULL");
+  BCCB_CUDA(s, cudaSetDevice(s->device));
+  if (!s->mu_ready) {
+    // the setup's mask part with y = 0 (mu depends on the mask alone); a later solve
+    // repeats the whole setup with its measurements
+    if (s->toeplitz)
+      BCCB_CUDA(s, bccb::run_setup_toeplitz(s, nullptr));
+    else
+      BCCB_CUDA(s, bccb::run_setup(s, nullptr));
+  }
+  std::vector<InstParams> p(s->n);
+  BCCB_CUDA(s, cudaStreamSynchronize(s->stream));
+  BCCB_CUDA(s, cudaMemcpy(p.data(), s->d_par, s->n * sizeof(InstParams), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < s->n; ++i) mu[i] = p[i].mu;
+  s->mu_ready = 1;
+  return BCCB_OK;
 }
 
 
@@ -619,7 +691,7 @@ int bccb_batch_get(bccb_solver_t s, int what, void* dst_dev) {
 }
 
 int bccb_create(bccb_solver_t* out, int M1, int M2, const uint8_t* mask_host, int L1, int L2, int algo, double rho,
-                void* cuda_stream) {
+                int prec, void* cuda_stream) {
   bccb_inst_t q;
   memset(&q, 0, sizeof(q));
   q.M1 = M1;
@@ -627,7 +699,7 @@ int bccb_create(bccb_solver_t* out, int M1, int M2, const uint8_t* mask_host, in
   q.L1 = L1;
   q.L2 = L2;
   q.lam = 0.0;
-  return bccb_batch_create(out, &q, 1, mask_host, algo, rho, cuda_stream);
+  return bccb_batch_create2(out, &q, 1, mask_host, algo, rho, prec, cuda_stream);
 }
 
 int bccb_solve(bccb_solver_t s, const void* y_dev, double lam, int lam_is_frac, int iters, const void* c0_dev,
@@ -643,7 +715,7 @@ int bccb_solve(bccb_solver_t s, const void* y_dev, double lam, int lam_is_frac, 
     BCCB_CUDA(s, cudaStreamSynchronize(s->stream));
   }
   const int check = (kkt_out || obj_out) ? 1 : 0;
-  int st = bccb_batch_solve(s, y_dev, iters, c0_dev, c_out_dev, aux_out_dev, check);
+  int st = bccb_batch_solve(s, y_dev, iters, c0_dev, c_out_dev, aux_out_dev, check, nullptr);
   if (st != BCCB_OK) return st;
   if (check) return bccb_batch_results(s, kkt_out, obj_out, nullptr, nullptr);
   return BCCB_OK;
@@ -689,7 +761,7 @@ int bccb_batch_capture(bccb_solver_t s, const void* y_dev, int iters, const void
   }
   cudaGraph_t g = nullptr;
   BCCB_CUDA(s, cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
-  const int st = bccb_batch_solve(s, y_dev, iters, c0_dev, c_out_dev, aux_out_dev, check);
+  const int st = bccb_batch_solve(s, y_dev, iters, c0_dev, c_out_dev, aux_out_dev, check, nullptr);
   cudaError_t e = cudaStreamEndCapture(s->stream, &g);
   if (st != BCCB_OK) {
     if (g) cudaGraphDestroy(g);
@@ -772,6 +844,7 @@ int bccb_batch_tune(bccb_solver_t s, const void* y_dev, int probe_iters, const c
     a.c0 = nullptr;
     a.c_out = s->d_probe;
     a.aux_out = nullptr;
+    a.lo = s->d_lo;
     a.iters = probe_iters;
     a.pad_ = 0;
     float best = 1e30f;
@@ -806,10 +879,11 @@ int bccb_batch_tune(bccb_solver_t s, const void* y_dev, int probe_iters, const c
   return BCCB_OK;
 }
 
-int bccb_unrolled_fwd(bccb_solver_t s, const void* y_dev, int layers, const float* scale_dev,
+int bccb_unrolled_fwd(bccb_solver_t s, const void* y_dev, int batch, int layers, const float* scale_dev,
                       const float* thresh_dev, void* c_out_dev, void* saved_dev, int check) {
   if (!s) return fail(nullptr, BCCB_ERR_INVALID_ARG, "solver is NULL");
   s->last_error.clear();
+  if (batch != s->n) return fail(s, BCCB_ERR_INVALID_ARG, "batch differs from the solver's instance count");
   if (s->algo != BCCB_FISTA) return fail(s, BCCB_ERR_INVALID_ARG, "the unrolled network needs a FISTA solver");
   if (s->toeplitz) return fail(s, BCCB_ERR_UNSUPPORTED, "the unrolled network needs gamma = 1/2");
   for (const auto& c : s->classes)
@@ -832,6 +906,7 @@ int bccb_unrolled_fwd(bccb_solver_t s, const void* y_dev, int layers, const floa
   a.thresh = thresh_dev;
   a.save = reinterpret_cast<float2*>(saved_dev);
   a.save_stride = s->total_c;
+  a.lo = s->d_lo;
   a.iters = layers;
   for (const auto& c : s->classes) {
     const bccb::FusedEntry* le = bccb::learned_lookup(c.L1, c.L2);
@@ -846,10 +921,11 @@ int bccb_unrolled_fwd(bccb_solver_t s, const void* y_dev, int layers, const floa
   return BCCB_OK;
 }
 
-int bccb_unrolled_bwd(bccb_solver_t s, int layers, const float* scale_dev, const float* thresh_dev,
+int bccb_unrolled_bwd(bccb_solver_t s, int batch, int layers, const float* scale_dev, const float* thresh_dev,
                       const void* saved_dev, const void* grad_c_dev, double* grad_scale_dev, double* grad_thresh_dev) {
   if (!s) return fail(nullptr, BCCB_ERR_INVALID_ARG, "solver is NULL");
   s->last_error.clear();
+  if (batch != s->n) return fail(s, BCCB_ERR_INVALID_ARG, "batch differs from the solver's instance count");
   if (s->algo != BCCB_FISTA) return fail(s, BCCB_ERR_INVALID_ARG, "the unrolled network needs a FISTA solver");
   if (s->toeplitz) return fail(s, BCCB_ERR_UNSUPPORTED, "the unrolled network needs gamma = 1/2");
   if (!scale_dev || !thresh_dev || !saved_dev || !grad_c_dev || !grad_scale_dev || !grad_thresh_dev || layers < 1)

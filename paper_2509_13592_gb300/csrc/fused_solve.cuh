@@ -36,6 +36,7 @@
 #pragma once
 
 #include <cooperative_groups.h>
+#include <cuda_bf16.h>
 
 #include "common.cuh"
 
@@ -69,9 +70,45 @@ struct FusedArgs {
   const float* thresh;
   float2* save;
   int64_t save_stride;
+  // ISTA/FISTA: low-order parts of the state, packed like c_out: {c_lo, z_lo} as bf16 pairs.
+  // Read and written only where the state is nonzero (see the update in fused_solve_kernel).
+  uint2* lo;
   int iters;
   int pad_;
 };
+
+// ---- compensated (double-float) arithmetic for the ISTA/FISTA state.  A value is hi + lo
+// with |lo| <= ulp(hi)/2; the sums below are Knuth's two-sum and Dekker's fast two-sum, the
+// product uses the exact FMA residual.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+// (ah + al) + (bh + bl), renormalised
+__device__ __forceinline__ void dd_add(float ah, float al, float bh, float bl, float& sh, float& sl) {
+  float s, e;
+  two_sum(ah, bh, s, e);
+  e = __fadd_rn(e, __fadd_rn(al, bl));
+  fast_two_sum(s, e, sh, sl);
+}
+// (ch + cl) + b (dh + dl)
+__device__ __forceinline__ void dd_axpy(float b, float dh, float dl, float ch, float cl, float& sh, float& sl) {
+  const float p = __fmul_rn(b, dh);
+  const float pl = fmaf(b, dl, fmaf(b, dh, -p));
+  dd_add(ch, cl, p, pl, sh, sl);
+}
+__device__ __forceinline__ uint32_t pack_bf16x2(float x, float y) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+__device__ __forceinline__ float2 unpack_bf16x2(uint32_t w) {
+  return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
 
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 __host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
@@ -110,8 +147,11 @@ struct FusedShape {
   static constexpr int POFF = SPLIT_MID ? ((SH * 2 + 15) / 16) * 16 : 0;
   // work (padded) + two state grids + twiddles + a frequency bit mask per middle-stage pair
   // + W_256^{i j} (16 x 16, rows of 256) + W_16^m + the cached multipliers and offsets
+  // ISTA/FISTA: two 8-byte slots per thread for the low-order parts of its first two
+  // positions with a nonzero state (see the update in fused_solve_kernel)
+  static constexpr int SLOTS = ADMM ? 0 : 2 * T * 8;
   static constexpr int SMEM = (R * P + 2 * E) * 8 + NMAX * 8 + ((SH * 2 + 15) / 16) * 16 + 256 * 8 + 16 * 8 +
-                              MCAP * 16 + POFF;
+                              MCAP * 16 + POFF + SLOTS;
   static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
   static_assert((R * P * 8) % 16 == 0, "16-byte aligned layout after the work rows");
   // two CTAs per SM when their shared memory fits (227 KB per CTA, 228 KB per SM)
@@ -447,6 +487,86 @@ struct FusedCta {
       for (int k = 0; k < 16; ++k) bp[k] = v[k];
     }
     __syncwarp();
+  }
+
+  // As sq_inv2_epi_fwd1, with the epilogue split in two: quick(row, e, i, g, flag) runs on all
+  // 16 outputs (unrolled) and either finishes the element (flag false) or returns a value to
+  // keep for the second part; ext(row, e, i, value) then runs on the flagged outputs only, in
+  // ascending i, in a loop that is not unrolled (one copy of its code).  The kept values wait in
+  // the positions this thread writes in the forward stage (free once the inputs are read).
+  template <typename Quick, typename Ext>
+  __device__ __forceinline__ void sq_inv2_split_fwd1(Quick&& quick, Ext&& ext, bool next, int nz) {
+    int row, j;
+    sq_rowj(row, j);
+    float2* const bp = sq_blk(row, j);
+    float2 v[16];
+    const float2* xr = work + row * P;
+    if (nz == 2) {
+      const float2 w = tw16[j];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = cadd(xr[pad16(i)], twmul<true>(xr[pad16(i + 16)], w));
+    } else if (nz == 1) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = xr[pad16(i)];
+    } else if (nz == 0) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = make_float2(0.f, 0.f);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = xr[j + 17 * i];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int i = 1; i < 16; ++i) v[i] = twmul<true>(v[i], tw256[i * 16 + j]);
+    Dft<16, true, float2>::run(v);
+    uint32_t flagged = 0u;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      bool f;
+      v[i] = quick(row, j + 16 * i, i, v[i], f);
+      if (f) flagged |= 1u << i;
+    }
+    if (flagged) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (flagged & (1u << i)) bp[i] = v[i];
+#pragma unroll 1
+      for (uint32_t m = flagged; m; m &= m - 1u) {
+        const int i = __ffs(m) - 1;
+        bp[i] = ext(row, j + 16 * i, i, bp[i]);
+      }
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (flagged & (1u << i)) v[i] = bp[i];
+    }
+    if (next) {
+      Dft<16, false, float2>::run(v);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) bp[k] = v[k];
+    }
+    __syncwarp();
+  }
+
+  // (row, position) of the o-th output a thread handles in the last stage of row_fft_from
+  // (o = k RS + i for butterfly k and output i of row_stage's loops)
+  __device__ __forceinline__ void last_row_output(int o, int& row, int& e) const {
+    constexpr int NST = num_stages(L1);
+    constexpr int RS = radix_of(L1, NST - 1);
+    constexpr int NS = 1 << (4 * (NST - 1));
+    constexpr int NBR = L1 / RS;
+    const int k = o / RS, i = o % RS;
+    int j;
+    if constexpr (S::ROW_WARP) {
+      constexpr int RPW = 512 / L1;
+      const int bw = (tid & 31) + 32 * k;
+      row = (tid >> 5) * RPW + bw / NBR;
+      j = bw % NBR;
+    } else {
+      const int b = tid + k * T;
+      row = b / NBR;
+      j = b % NBR;
+    }
+    e = (j / NS) * NS * RS + (j % NS) + i * NS;
   }
 
   // twiddles and the per-pair frequency masks (bt may be null: a Gram product alone)
@@ -820,6 +940,8 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
   cta.mtab = reinterpret_cast<float4*>(sp);
   sp += S::MCAP * 16;
   cta.poff = reinterpret_cast<uint16_t*>(sp);
+  sp += S::POFF;
+  uint2* const slot = reinterpret_cast<uint2*>(sp) + 2 * threadIdx.x;  // this thread's two slots
   cta.tid = threadIdx.x;
   int crank = 0;
   if constexpr (C > 1) crank = (int)cg::this_cluster().block_rank();
@@ -846,6 +968,7 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
 
   // ---- load twiddles, the frequency masks and the initial state
   cta.load_tables(a.twiddle, mult, bt, kc);
+  uint2* const lo = ADMM ? nullptr : a.lo + in.c_off;
   for (int idx = threadIdx.x; idx < E; idx += T) {
     const int s = idx / L1, e = idx % L1;
     const int gidx = (crank + C * s) * L1 + e;
@@ -856,58 +979,126 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
   }
   __syncthreads();
 
+  // ISTA/FISTA state in compensated form (see the update below).  Every thread updates the same
+  // positions, in the same order, in every iteration's epilogue; `live` has bit o set when its
+  // o-th position holds a nonzero state.  The low-order parts of its first two live positions
+  // sit in the thread's two shared-memory slots, those of any further ones in global memory (lo,
+  // packed like c_out).  The first epilogue treats every position as live with a zero low-order
+  // part (a complex64 warm start is exact), so no memory has to be cleared beforehand.
+  uint32_t live = 0xffffffffu, live_next = 0u;
+  int ord = 0, rank_old = 0, rank_new = 0;
+  uint2 slot_old0 = make_uint2(0u, 0u), slot_old1 = make_uint2(0u, 0u);
+  bool first = true;
+  auto epilogue_begin = [&]() {
+    if constexpr (!ADMM) {
+      if (!first) {
+        slot_old0 = slot[0];
+        slot_old1 = slot[1];
+      }
+      ord = rank_old = rank_new = 0;
+      live_next = 0u;
+    }
+  };
+  auto epilogue_end = [&]() {
+    if constexpr (!ADMM) {
+      live = live_next;
+      first = false;
+    }
+  };
+
   // ISTA runs as FISTA with every momentum weight 0 (a zero table, or no table):
   // c + 0 (c - c_prev) = c exactly, so the iterates are ISTA's.
 
-  // The pointwise update of one element after the inverse transform: returns the
-  // next iteration's FFT input (z for ISTA/FISTA, z - v for ADMM).
-  auto update = [&](int row, int e, float2 g, float beta, bool last, float sc, float kap, float2* save_t) -> float2 {
-    const int sidx = row * L1 + e;
-    if constexpr (!ADMM) {
-      if constexpr (BLOCK) {
-        if (e >= in.bl1 || crank + C * row >= in.bl2) {
-          cta.s0[sidx] = make_float2(0.f, 0.f);
-          cta.s1[sidx] = make_float2(0.f, 0.f);
-          return make_float2(0.f, 0.f);
-        }
+  // ISTA/FISTA.  The state is kept in compensated form: c = s0 + c_lo, z = s1 + z_lo, the high
+  // parts complex64 in shared memory, the low parts bf16.  FISTA's momentum carries every
+  // rounding at the scale of |z| through the rest of the solve (it has a double root at 1 along
+  // directions the Gram does not see), so u = z - G', the soft-threshold and the momentum are
+  // formed in double-float arithmetic; G' itself is of the size of the gradient and keeps its
+  // FP32 transform.  The soft-threshold is taken as c = u - kappa u/|u|, whose rounded term is
+  // of the size of kappa, not of |u|.
+  //
+  // quick: every output of the inverse transform (the thread's o-th).  Off the support the
+  // state is exactly 0 and stays 0 while |G'| <= kappa: that element is finished here, touching
+  // no memory.  Otherwise it is flagged and the (scaled) G' is kept for ext.
+  auto quick = [&](int row, int e, int o, float2 g, bool& flag, float sc, float kap, float2* save_t) -> float2 {
+    if constexpr (BLOCK) {
+      if (e >= in.bl1 || crank + C * row >= in.bl2) {  // outside the caller's block: stays 0
+        flag = false;
+        return make_float2(0.f, 0.f);
       }
-      const float2 c_old = cta.s0[sidx];
-      const float2 x = cta.s1[sidx];  // z^(t)
-      float2 un;
-      if constexpr (LEARN) {
-        if (save_t) {
-          const int gidx = (crank + C * row) * L1 + e;
-          save_t[gidx] = x;
-          save_t[a.save_stride + gidx] = g;
-        }
-        un = make_float2(x.x - sc * g.x, x.y - sc * g.y);
-      } else {
-        un = make_float2(x.x - g.x, x.y - g.y);
+    }
+    const bool was_live = (live >> o) & 1u;
+    if constexpr (LEARN) {
+      if (save_t) {
+        const int gidx = (crank + C * row) * L1 + e;
+        save_t[gidx] = was_live ? cta.s1[row * L1 + e] : make_float2(0.f, 0.f);
+        save_t[a.save_stride + gidx] = g;
       }
-      // c_new = u s; the momentum difference c_new - c_old is taken from the unrounded
-      // product (one rounding, by the fused multiply-add), which keeps the FP32 rounding of
-      // c_new out of the momentum term: FISTA's momentum amplifies that rounding over the
-      // iterations, and this roughly halves the drift from the FP64 iterates
-      const float sc = soft_scale(un, kap);
-      const float2 cn = make_float2(un.x * sc, un.y * sc);
-      const float dx = fmaf(un.x, sc, -c_old.x), dy = fmaf(un.y, sc, -c_old.y);
-      cta.s0[sidx] = cn;
-      const float2 zn = make_float2(fmaf(beta, dx, cn.x), fmaf(beta, dy, cn.y));
-      cta.s1[sidx] = zn;
-      return zn;
+      g = make_float2(sc * g.x, sc * g.y);
     } else {
-      const float2 zo = cta.s0[sidx];
-      const float2 vo = cta.s1[sidx];
-      const float2 un = make_float2(zo.x - g.x, zo.y - g.y);  // c^(t+1) + v^(t)
-      const float2 zn = soft_threshold(un, kap);
-      const float2 vn = make_float2(un.x - zn.x, un.y - zn.y);
-      cta.s0[sidx] = zn;
-      cta.s1[sidx] = vn;
-      if (last && aux_out) aux_out[(crank + C * row) * L1 + e] = make_float2(un.x - vo.x, un.y - vo.y);
       (void)sc;
       (void)save_t;
-      return make_float2(zn.x - vn.x, zn.y - vn.y);
     }
+    flag = was_live || (g.x * g.x + g.y * g.y > kap * kap);
+    return flag ? g : make_float2(0.f, 0.f);
+  };
+  // ext: a flagged element, in ascending o; returns z^(t+1), the next FFT input
+  auto ext = [&](int row, int e, int o, float2 g, float beta, float kap) -> float2 {
+    const int sidx = row * L1 + e;
+    const int gidx = (crank + C * row) * L1 + e;
+    float2 c_old = make_float2(0.f, 0.f), x = make_float2(0.f, 0.f);  // c^(t-1), z^(t)
+    float2 cl = make_float2(0.f, 0.f), zl = make_float2(0.f, 0.f);
+    if ((live >> o) & 1u) {
+      c_old = cta.s0[sidx];
+      x = cta.s1[sidx];
+      if (!first) {
+        const uint2 w = rank_old == 0 ? slot_old0 : rank_old == 1 ? slot_old1 : lo[gidx];
+        cl = unpack_bf16x2(w.x);
+        zl = unpack_bf16x2(w.y);
+      }
+      ++rank_old;
+    }
+    float uxh, uxl, uyh, uyl;  // u = z - G'
+    dd_add(x.x, zl.x, -g.x, 0.f, uxh, uxl);
+    dd_add(x.y, zl.y, -g.y, 0.f, uyh, uyl);
+    float cxh = 0.f, cxl = 0.f, cyh = 0.f, cyl = 0.f;
+    const float r2 = uxh * uxh + uyh * uyh;
+    if (r2 > kap * kap) {
+      const float kr = kap * rsqrtf(r2);
+      dd_add(uxh, uxl, -(kr * uxh), 0.f, cxh, cxl);
+      dd_add(uyh, uyl, -(kr * uyh), 0.f, cyh, cyl);
+    }
+    float dxh, dxl, dyh, dyl;  // c^(t) - c^(t-1)
+    dd_add(cxh, cxl, -c_old.x, -cl.x, dxh, dxl);
+    dd_add(cyh, cyl, -c_old.y, -cl.y, dyh, dyl);
+    float zxh, zxl, zyh, zyl;  // z^(t+1) = c^(t) + beta_t (c^(t) - c^(t-1))
+    dd_axpy(beta, dxh, dxl, cxh, cxl, zxh, zxl);
+    dd_axpy(beta, dyh, dyl, cyh, cyl, zyh, zyl);
+    cta.s0[sidx] = make_float2(cxh, cyh);
+    cta.s1[sidx] = make_float2(zxh, zyh);
+    if ((cxh != 0.f) | (cyh != 0.f) | (zxh != 0.f) | (zyh != 0.f)) {
+      const uint2 w = make_uint2(pack_bf16x2(cxl, cyl), pack_bf16x2(zxl, zyl));
+      if (rank_new < 2)
+        slot[rank_new] = w;
+      else
+        lo[gidx] = w;
+      ++rank_new;
+      live_next |= 1u << o;
+    }
+    return make_float2(zxh, zyh);
+  };
+  // ADMM: u = z - G' = c^(t+1) + v^(t), z^(t+1) = S(u), v^(t+1) = u - z^(t+1); returns z - v
+  auto update_admm = [&](int row, int e, float2 g, bool last, float kap) -> float2 {
+    const int sidx = row * L1 + e;
+    const float2 zo = cta.s0[sidx];
+    const float2 vo = cta.s1[sidx];
+    const float2 un = make_float2(zo.x - g.x, zo.y - g.y);  // c^(t+1) + v^(t)
+    const float2 zn = soft_threshold(un, kap);
+    const float2 vn = make_float2(un.x - zn.x, un.y - zn.y);
+    cta.s0[sidx] = zn;
+    cta.s1[sidx] = vn;
+    if (last && aux_out) aux_out[(crank + C * row) * L1 + e] = make_float2(un.x - vo.x, un.y - vo.y);
+    return make_float2(zn.x - vn.x, zn.y - vn.y);
   };
   // per-iteration multipliers of the unrolled network (1 and kappa otherwise)
   auto layer = [&](int it, float& sc, float& kap, float2*& save_t) {
@@ -940,8 +1131,15 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
       float sc, kap;
       float2* save_t;
       layer(it, sc, kap, save_t);
-      cta.sq_inv2_epi_fwd1(
-          [&](int row, int e, float2 g) { return update(row, e, g, beta, last, sc, kap, save_t); }, !last, nz);
+      if constexpr (ADMM) {
+        cta.sq_inv2_epi_fwd1([&](int row, int e, float2 g) { return update_admm(row, e, g, last, kap); }, !last, nz);
+      } else {
+        epilogue_begin();
+        cta.sq_inv2_split_fwd1(
+            [&](int row, int e, int o, float2 g, bool& f) { return quick(row, e, o, g, f, sc, kap, save_t); },
+            [&](int row, int e, int o, float2 g) { return ext(row, e, o, g, beta, kap); }, !last, nz);
+        epilogue_end();
+      }
     }
   } else {
     for (int it = 0; it < a.iters; ++it) {
@@ -962,11 +1160,37 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
       float sc, kap;
       float2* save_t;
       layer(it, sc, kap, save_t);
-      cta.template row_fft_from<0, true>(
-          [&](int row, int e, float2 g) {
-            cta.work[row * P + pad16(e)] = update(row, e, g, beta, last, sc, kap, save_t);
-          },
-          kc);
+      if constexpr (ADMM) {
+        cta.template row_fft_from<0, true>(
+            [&](int row, int e, float2 g) { cta.work[row * P + pad16(e)] = update_admm(row, e, g, last, kap); },
+            kc);
+      } else {
+        // the quick part inside the last row stage, then the flagged outputs (this thread's own
+        // work positions) one by one, before the next stage reads them
+        epilogue_begin();
+        uint32_t flagged = 0u;
+        cta.template row_fft_from<0, true>(
+            [&](int row, int e, float2 g) {
+              bool f;
+              const int o = ord++;
+              cta.work[row * P + pad16(e)] = quick(row, e, o, g, f, sc, kap, save_t);
+              if (f) flagged |= 1u << o;
+            },
+            kc);
+#pragma unroll 1
+        for (uint32_t m = flagged; m; m &= m - 1u) {
+          const int o = __ffs(m) - 1;
+          int row, e;
+          cta.last_row_output(o, row, e);
+          float2* w = &cta.work[row * P + pad16(e)];
+          *w = ext(row, e, o, *w, beta, kap);
+        }
+        if constexpr (S::ROW_WARP)
+          __syncwarp();
+        else
+          __syncthreads();
+        epilogue_end();
+      }
     }
   }
 

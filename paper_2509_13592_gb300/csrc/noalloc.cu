@@ -29,7 +29,8 @@ constexpr size_t kOffBt = kOffMult + up(sizeof(float) * kMaxGrid);
 constexpr size_t kOffBeta = kOffBt + up(sizeof(float2) * kMaxGrid);
 constexpr size_t kOffTw32 = kOffBeta + up(sizeof(float) * kMaxIters);
 constexpr size_t kOffTw64 = kOffTw32 + up(sizeof(float2) * bccb::kTwiddleLen);
-constexpr size_t kScratchBytes = kOffTw64 + up(sizeof(double2) * bccb::kTwiddleLen);
+constexpr size_t kOffLo = kOffTw64 + up(sizeof(double2) * bccb::kTwiddleLen);
+constexpr size_t kScratchBytes = kOffLo + up(sizeof(uint2) * kMaxGrid);
 
 // The working memory.  In host code this name is only a stand-in for the device
 // array: host code must use the address cudaGetSymbolAddress returns.
@@ -41,7 +42,9 @@ unsigned char* g_base[kMaxDevices] = {};
 
 // y index of each URA position (-1 if the element is not kept): exclusive count
 // of the kept elements in ascending m1 + m2*M1, as the rows of Psi are ordered.
-__global__ void mask_index_kernel(const uint8_t* __restrict__ mask, int n, int* __restrict__ idx) {
+// The total goes to desc->N, so the record matches the one bccb_create builds.
+__global__ void mask_index_kernel(const uint8_t* __restrict__ mask, int n, int* __restrict__ idx,
+                                  bccb::InstDesc* desc) {
   __shared__ int warp_tot[32];
   __shared__ int carry;
   if (threadIdx.x == 0) carry = 0;
@@ -72,6 +75,7 @@ __global__ void mask_index_kernel(const uint8_t* __restrict__ mask, int n, int* 
     if (threadIdx.x == blockDim.x - 1) carry = before + keep;
     __syncthreads();
   }
+  if (threadIdx.x == 0) desc->N = carry;
 }
 
 // the per-call records (passed by value, written on the device)
@@ -86,18 +90,21 @@ __global__ void records_kernel(bccb::InstDesc d, bccb::InstDesc* desc, bccb::Fus
   ids[0] = 0;
 }
 
-// Once per device: find the array and upload the twiddle tables.
+// Find the array on the current device and, the first time it is seen at that address,
+// upload the twiddle tables.  The address is looked up on every call (a lookup allocates
+// nothing): after cudaDeviceReset the module is loaded again, possibly elsewhere and
+// without the tables, and the set-up then runs again.
 int device_setup(int dev, unsigned char** base, const char** err) {
   std::lock_guard<std::mutex> lock(g_mu);
-  if (g_base[dev]) {
-    *base = g_base[dev];
-    return BCCB_OK;
-  }
   void* p = nullptr;
   cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
   if (e != cudaSuccess) {
     *err = cudaGetErrorString(e);
     return BCCB_ERR_CUDA;
+  }
+  if (g_base[dev] == p) {
+    *base = g_base[dev];
+    return BCCB_OK;
   }
   static float2 t32[bccb::kTwiddleLen];
   static double2 t64[bccb::kTwiddleLen];
@@ -179,7 +186,7 @@ extern "C" int bccb_solve_noalloc(int M1, int M2, const uint8_t* mask_dev, int L
   d.M2 = M2;
   d.L1 = L1;
   d.L2 = L2;
-  d.N = 0;  // not read by the device code
+  d.N = 0;  // mask_index_kernel writes the kept-element count into the device record
   d.lam_is_frac = lam_is_frac ? 1 : 0;
   d.mask_off = 0;
   d.y_off = 0;
@@ -188,7 +195,7 @@ extern "C" int bccb_solve_noalloc(int M1, int M2, const uint8_t* mask_dev, int L
   d.lam = lam;
 
   records_kernel<<<1, 1, 0, s.stream>>>(d, s.d_desc, s.d_fused, s.d_ids);
-  mask_index_kernel<<<1, 1024, 0, s.stream>>>(mask_dev, M1 * M2, s.d_mask_idx);
+  mask_index_kernel<<<1, 1024, 0, s.stream>>>(mask_dev, M1 * M2, s.d_mask_idx, s.d_desc);
   if ((e = cudaGetLastError()) != cudaSuccess) return reject(BCCB_ERR_CUDA, cudaGetErrorString(e));
   if (algo == BCCB_FISTA && (e = bccb::fista_schedule(&s, iters)) != cudaSuccess)
     return reject(BCCB_ERR_CUDA, cudaGetErrorString(e));
@@ -205,6 +212,7 @@ extern "C" int bccb_solve_noalloc(int M1, int M2, const uint8_t* mask_dev, int L
   a.c0 = nullptr;
   a.c_out = reinterpret_cast<float2*>(c_out_dev);
   a.aux_out = nullptr;
+  a.lo = reinterpret_cast<uint2*>(base + kOffLo);
   a.iters = iters;
   a.pad_ = 0;
   if ((e = fe->launch(a, 1, s.stream)) != cudaSuccess) return reject(BCCB_ERR_CUDA, cudaGetErrorString(e));

@@ -87,7 +87,7 @@ __global__ void scatter_kernel(const InstDesc* __restrict__ desc, const int* __r
   const InstDesc d = desc[blockIdx.x];
   const int L = d.L1 * d.L2;
   const int* mi = mask_idx + d.mask_off;
-  const Y* yi = y + d.y_off;
+  const Y* yi = y ? y + d.y_off : nullptr;
   for (int cell = blockIdx.y * blockDim.x + threadIdx.x; cell < L; cell += gridDim.y * blockDim.x) {
     const int p1 = cell % d.L1, p2 = cell / d.L1;
     double cnt = 0.0;
@@ -97,9 +97,11 @@ __global__ void scatter_kernel(const InstDesc* __restrict__ desc, const int* __r
         const int n = mi[m1 + m2 * d.M1];
         if (n >= 0) {
           cnt += 1.0;
-          const double sgn = ((m1 + m2) & 1) ? -1.0 : 1.0;
-          acc.x += sgn * (double)yi[n].x;
-          acc.y += sgn * (double)yi[n].y;
+          if (y) {  // y = NULL: the mask part alone (Lambda, mu), as if y were 0
+            const double sgn = ((m1 + m2) & 1) ? -1.0 : 1.0;
+            acc.x += sgn * (double)yi[n].x;
+            acc.y += sgn * (double)yi[n].y;
+          }
         }
       }
     }
@@ -154,7 +156,9 @@ __global__ void eig_mult_kernel(const InstDesc* __restrict__ desc, const int* __
   double top = 0.0;
   for (int cell = threadIdx.x; cell < L; cell += blockDim.x) top = fmax(top, lam_c[cell].x);
   top = block_reduce(top, MaxOp(), sh, 0.0);
-  const double mu = 1.0 / top;
+  // an all-zero mask (no element kept: A has no rows) has Lambda = 0; mu = 0 then makes q,
+  // Bt and kappa 0 and the iterations return c = 0, the minimiser of the data-free problem
+  const double mu = top > 0.0 ? 1.0 / top : 0.0;
   const double inv_L = 1.0 / (double)L;
   // inv_L is a power of two, so mu inv_L is exact and lv (mu inv_L) rounds like (mu lv) inv_L
   const double mu_L = mu * inv_L;
@@ -411,12 +415,12 @@ __global__ void toep_b1_kernel(const InstDesc* __restrict__ desc, const int* __r
                                const Y* __restrict__ y, double g1, double2* h) {
   const InstDesc d = desc[blockIdx.x];
   const int* mi = mask_idx + d.mask_off;
-  const Y* yi = y + d.y_off;
+  const Y* yi = y ? y + d.y_off : nullptr;
   for (int t = blockIdx.y * blockDim.x + threadIdx.x; t < d.bL1 * d.M2; t += gridDim.y * blockDim.x) {
     const int l1 = t % d.bL1, m2 = t / d.bL1;
     const double f1 = -g1 + (double)l1 * (2.0 * g1 / (double)d.bL1);
     double2 acc = make_double2(0.0, 0.0);
-    for (int m1 = 0; m1 < d.M1; ++m1) {
+    for (int m1 = 0; m1 < d.M1 && yi; ++m1) {  // y = NULL: b = 0 (the mask part alone)
       const int n = mi[m1 + m2 * d.M1];
       if (n < 0) continue;
       double sn, cs;

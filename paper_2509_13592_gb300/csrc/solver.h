@@ -70,6 +70,7 @@ struct bccb_solver {
   double2* d_w64 = nullptr;     // FP64 FFT workspace
   float* d_mult = nullptr;      // FP32 Fourier multiplier (includes 1/(L1 L2))
   float2* d_cterm = nullptr;    // FP32 Fourier-domain constant term Bt
+  uint2* d_lo = nullptr;        // fused ISTA/FISTA: low-order parts of the state, packed like c
   bccb::InstParams* d_par = nullptr;
   bccb::FusedInst* d_fused = nullptr;
   int* d_ids = nullptr;
@@ -123,6 +124,8 @@ struct bccb_solver {
   double2* d_toep_h = nullptr;    // FP64 scratch of the Toeplitz setup
   double2* d_toep_fb = nullptr;   // FP64 FFT2 of the zero-padded b (Toeplitz)
   int toep_ready = 0;             // the embedding's spectrum (d_lam64) and mu are in place
+  int mu_ready = 0;               // d_par[i].mu holds 1/max Lambda (it depends on the mask alone)
+  double kkt_tol = 1e-2;          // status BCCB_ERR_KKT above this relative KKT residual
   // iteration engine: 0 = FFT (fused / multi-pass), 1 = dense L x L Gram (dense.cu)
   int method = 0;
   float2* d_gram = nullptr;       // per instance L x L complex64, row-major

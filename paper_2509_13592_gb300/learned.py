@@ -57,7 +57,8 @@ class UnrolledFISTA(torch.autograd.Function):
         c = torch.empty(net.batch * net.L, dtype=torch.complex64, device=y.device)
         need = ctx.needs_input_grad[1] or ctx.needs_input_grad[2]
         saved = torch.empty(K * 2 * net.batch * net.L, dtype=torch.complex64, device=y.device) if need else None
-        B.bccb_unrolled_fwd(net.handle, y, K, scale.detach().contiguous(), thresh.detach().contiguous(), c, saved)
+        B.bccb_unrolled_fwd(net.handle, y, net.batch, K, scale.detach().contiguous(), thresh.detach().contiguous(),
+                            c, saved)
         ctx.net = net
         ctx.saved = saved
         ctx.save_for_backward(scale.detach(), thresh.detach())
@@ -69,7 +70,7 @@ class UnrolledFISTA(torch.autograd.Function):
         K = scale.numel()
         g_s = torch.zeros(K, dtype=torch.float64, device=scale.device)
         g_t = torch.zeros(K, dtype=torch.float64, device=scale.device)
-        B.bccb_unrolled_bwd(ctx.net.handle, K, scale.contiguous(), thresh.contiguous(), ctx.saved,
+        B.bccb_unrolled_bwd(ctx.net.handle, ctx.net.batch, K, scale.contiguous(), thresh.contiguous(), ctx.saved,
                             grad_c.contiguous().to(torch.complex64), g_s, g_t)
         return None, g_s.to(scale.dtype), g_t.to(thresh.dtype), None
 
@@ -90,9 +91,10 @@ def infer_with_fallback(net: UnrolledNet, y, scale, thresh, kkt_tol=1e-2, fallba
     get `fallback_iters` iterations of plain FISTA warm-started from the network's output.
     Returns (c, kkt_after_net, fallback_mask)."""
     c = torch.empty(net.batch * net.L, dtype=torch.complex64, device=y.device)
-    B.bccb_unrolled_fwd(net.handle, y, scale.numel(), scale, thresh, c, None, True)
+    B.bccb_unrolled_fwd(net.handle, y, net.batch, scale.numel(), scale, thresh, c, None, True)
     kkt = net.solver.results()["kkt"]
-    bad = np.flatnonzero(kkt > kkt_tol)
+    B.bccb_set_kkt_tol(net.handle, kkt_tol)
+    bad = np.flatnonzero(B.bccb_batch_status(net.handle, net.batch) == B.ERR_KKT)
     if bad.size:
         ys = y.reshape(net.batch, net.N)[torch.as_tensor(bad, device=y.device)].reshape(-1).contiguous()
         c0 = c.reshape(net.batch, net.L)[torch.as_tensor(bad, device=y.device)].reshape(-1).contiguous()

@@ -1,26 +1,20 @@
 """Parity at the benchmark's full size and launch configuration: 4096 snapshots of the
 256x256 workload (32x32 array, N = 256, 8 off-grid sources, 10 dB, lam = 0.05 ||A^H y||_inf),
 FISTA x 1000 in one batched solve with the autotuned tile, captured and replayed as bench.py
-times it.  The oracle solves 16 evenly spaced instances one by one.
-
-FP32 and 1000 momentum iterations: FISTA amplifies the per-iteration FP32 rounding (about
-1000-fold over the run on this workload), so the error against the FP64 iterates is a
-distribution, not a constant.  A plain float32 emulation of the same iteration shows the same
-spread, with a tail to about 3e-4 on instances where an entry sits at the threshold.  The bar
-of 1e-4 therefore applies to the sample median, every sample must stay within the FP32 tail
-(5e-4), and the full check (including the support) runs on every sample within 1e-4."""
+times it.  The oracle solves 64 evenly spaced instances one by one; every one of them is held
+to the parity bar (relative l2 error <= 1e-4, identical support apart from entries within
+1e-5 of the threshold)."""
 import numpy as np
 import pytest
 
 import oracle
 import synth
-from gpu_util import REL_TOL, assert_parity, inst, rel_err
+from gpu_util import assert_parity, inst
 
 pytestmark = pytest.mark.gpu
 
 B, T = 4096, 1000
-SAMPLES = tuple(range(0, B, B // 16))[:15] + (B - 1,)
-FP32_TAIL = 5e-4
+SAMPLES = tuple(range(0, B, B // 64))[:63] + (B - 1,)
 
 
 def _snap(i):
@@ -53,13 +47,7 @@ def test_full_size_batch_sampled_against_oracle(lib):
         assert lam == pytest.approx(0.05 * oracle.lambda_max(A, y32), rel=1e-9)
         c_ref, u, kappa = oracle.fista(A, y32, lam, T, pre=True)
         got = grids[i].reshape(-1)
-        err = rel_err(got, c_ref)
-        errs.append(err)
-        assert err <= FP32_TAIL, f"instance {i}: relative error {err:.2e} beyond the FP32 tail"
-        if err <= REL_TOL:
-            assert_parity(got, dict(c=c_ref, u=u, kappa=kappa), what=f"instance {i} of the full batch")
+        errs.append(assert_parity(got, dict(c=c_ref, u=u, kappa=kappa), what=f"instance {i} of the full batch"))
         assert res["kkt"][i] == pytest.approx(oracle.kkt_residual(A, y32, got.astype(np.complex128), lam),
                                               rel=1e-6, abs=1e-9)
-    med = float(np.median(errs))
-    print("relative errors:", " ".join(f"{e:.1e}" for e in errs), f"median {med:.1e}")
-    assert med <= REL_TOL, f"median relative error {med:.2e} over {len(errs)} sampled instances"
+    print(f"relative errors over {len(errs)} instances: median {np.median(errs):.1e}, max {max(errs):.1e}")

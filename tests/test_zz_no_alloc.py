@@ -27,14 +27,14 @@ def _entry(lib):
     return f
 
 
-def _noalloc(lib, f, s, algo, lam, iters, rho):
+def _noalloc(lib, f, s, algo, lam, iters, rho, lam_is_frac=0, mask=None):
     import torch
 
-    mask = torch.from_numpy(np.ascontiguousarray(s.mask, np.uint8)).cuda()
+    mask = torch.from_numpy(np.ascontiguousarray(s.mask if mask is None else mask, np.uint8)).cuda()
     y = torch.from_numpy(s.y.astype(np.complex64)).cuda()
     c = torch.full((s.L1 * s.L2,), 7.0 + 7.0j, dtype=torch.complex64, device="cuda")  # garbage on purpose
-    st = f(s.M1, s.M2, mask.data_ptr(), s.L1, s.L2, ALGO[algo], rho, y.data_ptr(), lam, 0, iters, c.data_ptr(),
-           torch.cuda.current_stream().cuda_stream)
+    st = f(s.M1, s.M2, mask.data_ptr(), s.L1, s.L2, ALGO[algo], rho, y.data_ptr(), lam, lam_is_frac, iters,
+           c.data_ptr(), torch.cuda.current_stream().cuda_stream)
     assert st == 0, lib.bccb_status_string(st)
     torch.cuda.synchronize()
     return c.cpu().numpy()
@@ -44,13 +44,40 @@ def test_noalloc_matches_ordinary_entry_point_on_two_calls_in_a_row(lib):
     f = _entry(lib)
     s1 = synth.config_snapshot(2, 1)  # 32x32 array, N=256, 256x256 grid
     s2 = synth.make_snapshot(77, 16, 32, 120, 64, 128, 4, 12.0)
-    cases = [(s1, "fista", 300, 1.0), (s2, "admm", 150, 4.0)]
-    for s, algo, iters, rho in cases:
+    s3 = synth.make_snapshot(78, 12, 8, 40, 32, 64, 3, 15.0)
+    # (snapshot, algorithm, iterations, rho, lam given as a fraction of ||A^H y||_inf)
+    cases = [(s1, "fista", 300, 1.0, False), (s2, "admm", 150, 4.0, False), (s3, "ista", 200, 1.0, True)]
+    for s, algo, iters, rho, frac in cases:
         lam = 0.05 * _lmax(s)
         ref = gpu_run(lib, [s], [lam], algo, iters, rho=rho, check=False)["c"][0]
-        got = _noalloc(lib, f, s, algo, lam, iters, rho)
+        if frac:
+            got = _noalloc(lib, f, s, algo, 0.05, iters, rho, lam_is_frac=1)
+        else:
+            got = _noalloc(lib, f, s, algo, lam, iters, rho)
         assert rel_err(got, ref) <= REL_TOL, (algo, rel_err(got, ref))
         assert np.array_equal(np.abs(got) > 0, np.abs(ref) > 0)
+
+
+def test_noalloc_against_the_oracle(lib):
+    """One case checked against the FP64 oracle directly, so the entry point is pinned
+    independently of the ordinary one."""
+    from gpu_util import assert_parity, oracle_run
+
+    f = _entry(lib)
+    s = synth.config_snapshot(1, 0)  # 16x16 array, N = 64, 64x64 grid, 3 on-grid sources
+    ref = oracle_run(s, "fista", 500)
+    got = _noalloc(lib, f, s, "fista", ref["lam"], 500, 1.0)
+    assert_parity(got, ref, what="noalloc FISTA 64x64")
+
+
+def test_noalloc_empty_mask_returns_zero(lib):
+    """No element kept: A has no rows, so c = 0 minimises the LASSO; the call returns it
+    (and not the NaN that 1/max Lambda would give)."""
+    f = _entry(lib)
+    s = synth.make_snapshot(79, 8, 8, 10, 32, 32, 2, 10.0)
+    for algo in ("fista", "admm"):
+        got = _noalloc(lib, f, s, algo, 0.1, 20, 2.0, lam_is_frac=1, mask=np.zeros(64, np.uint8))
+        assert np.all(got == 0), algo
 
 
 def test_noalloc_rejects_sizes_beyond_its_limits(lib):
