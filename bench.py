@@ -480,20 +480,33 @@ def run_workload(args):
                 "grid_elements": elems, "flop_rate_tflops": sum(flops_per_inst_iter(s.L1, s.L2) for s in snaps)
                 * T / (t["iterate_ms"] / 1e3) / 1e12}
     elif args.workload == "precision1024":
+        # the precision study at full length: FP32 and FP64 GPU paths, ADMM x 2000 at the stated rho = 0.5
+        # and at rho = N = 1024, each result's error against the stored FP64 oracle reference
+        sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
+        import make_admm1024 as golden
+
         s = synth.config_snapshot(4, 0)
+        s.y = s.y.astype(np.complex64).astype(np.complex128)  # the measurements the reference was given
         inst = [dict(M1=s.M1, M2=s.M2, L1=s.L1, L2=s.L2, mask=s.mask, y=s.y, lam=0.05, lam_is_frac=True)]
-        T = args.iters
-        (c32, a32), t32, r32 = _solve_timed(bccb, torch, inst, "admm", T, rho=0.5, prec="f32", reps=1, check=True)
-        (c64, a64), t64, r64 = _solve_timed(bccb, torch, inst, "admm", T, rho=0.5, prec="f64", reps=1, check=True)
-        n64 = np.linalg.norm(c64)
-        line = {"workload": f"1024x1024 grid, 64x64 array N=1024, 20 off-grid sources, 15 dB, ADMM rho=0.5, "
-                            f"lam=0.05||A^H y||_inf, {T} iterations, single snapshot",
-                "fp32_ms": t32, "fp64_ms": t64,
-                "rel_err_z_fp32_vs_fp64": float(np.linalg.norm(c32 - c64) / n64) if n64 > 0 else None,
-                "rel_err_c_fp32_vs_fp64": float(np.linalg.norm(a32 - a64) / np.linalg.norm(a64)),
-                "nnz_fp32": int(np.count_nonzero(c32)), "nnz_fp64": int(np.count_nonzero(c64)),
-                "kkt_fp32": float(r32["kkt"][0]), "kkt_fp64": float(r64["kkt"][0]),
-                "objective_fp32": float(r32["objective"][0]), "objective_fp64": float(r64["objective"][0])}
+        T = golden.ITERS
+        studies = []
+        for tag in ("0p5", "1024"):
+            ref = golden.read(tag)
+            row = {"rho": ref["rho"], "norm_z": ref["norm_z"], "norm_c": ref["norm_c"], "norm_v": ref["norm_v"],
+                   "oracle_nonzeros_z": int(ref["z_idx"].size)}
+            for prec in ("f32", "f64"):
+                (z, c), t, r = _solve_timed(bccb, torch, inst, "admm", T, rho=ref["rho"], prec=prec, reps=1,
+                                            check=True)
+                row[prec] = {"ms": t, "rel_err_vs_oracle": golden.errors(z.astype(np.complex128),
+                                                                          c.astype(np.complex128), ref),
+                             "nonzeros_z": int(np.count_nonzero(z)), "kkt": float(r["kkt"][0]),
+                             "objective": float(r["objective"][0])}
+            studies.append(row)
+        line = {"workload": f"1024x1024 grid, 64x64 array N=1024, 20 off-grid sources, 15 dB, lam=0.05||A^H y||_inf, "
+                            f"ADMM {T} iterations, single snapshot; rho = 0.5 (stated) and rho = N",
+                "reference": "FP64 oracle (tests/golden/admm1024_rho*.txt): z^(T) in full, c^(T) on 1024 sampled "
+                             "entries and in norm",
+                "studies": studies}
     elif args.workload == "peaks":
         # harmonic / angle extraction (Section II-A) on the solutions of the batched 256x256 workload
         B, T, K = args.batch, args.iters, 16

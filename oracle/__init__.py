@@ -28,6 +28,8 @@ from .lasso import (  # noqa: F401
     fista_momentum,
     admm,
     admm_c_update,
+    admm_kron,
+    KronDictionary,
     kkt_residual,
     objective,
     gram_first_column,

@@ -88,6 +88,66 @@ def adjoint_measurements_kron(mask, M1: int, M2: int, L1: int, L2: int, y) -> np
     return (D2s.conj().T @ (y[:, None] * D1s.conj())).reshape(-1)
 
 
+class KronDictionary:
+    """D_s = Psi (D2 kron D1) applied through its Kronecker factors, for grids too large to
+    form (eq:forward_model, eq:sparse_forward_model): with a grid W[l2, l1] (the vector
+    c[l1 + l2 L1]),
+      (D_s c)_n   = (D2 W D1^T)[m2_n, m1_n],
+      (D_s^H r)   = D2^H R conj(D1),  R[m2, m1] = sum of r_n over the elements at (m1, m2),
+      (D_s D_s^H) = (D1 D1^H)[m1_n, m1_n'] * (D2 D2^H)[m2_n, m2_n']  (entrywise),
+    with D_i the full M_i x L_i subdictionaries of eq:subdictionary.  These are the dense
+    products regrouped by the Kronecker structure (matrix products only, no FFT)."""
+
+    def __init__(self, mask, M1: int, M2: int, L1: int, L2: int):
+        self.M1, self.M2, self.L1, self.L2 = M1, M2, L1, L2
+        self.m1, self.m2 = element_positions(mask, M1)
+        self.D1 = np.exp(-2j * np.pi * np.outer(np.arange(M1), harmonic_grid(L1)))
+        self.D2 = np.exp(-2j * np.pi * np.outer(np.arange(M2), harmonic_grid(L2)))
+        self.shape = (self.m1.size, L1 * L2)
+
+    def forward(self, c):
+        W = np.asarray(c, np.complex128).reshape(self.L2, self.L1)
+        return (self.D2 @ W @ self.D1.T)[self.m2, self.m1]
+
+    def adjoint(self, r):
+        R = np.zeros((self.M2, self.M1), np.complex128)
+        np.add.at(R, (self.m2, self.m1), np.asarray(r, np.complex128))
+        return (self.D2.conj().T @ R @ self.D1.conj()).reshape(-1)
+
+    def gram_rows(self):
+        S1 = self.D1 @ self.D1.conj().T
+        S2 = self.D2 @ self.D2.conj().T
+        return S1[np.ix_(self.m1, self.m1)] * S2[np.ix_(self.m2, self.m2)]
+
+
+def admm_kron(K: KronDictionary, y, lam, rho, iters):
+    """ADMM (eq:admm) exactly as ``admm``, with every product with D_s taken through its
+    Kronecker factors (``KronDictionary``) and the Woodbury form of (A^H A + rho I)^{-1} on
+    the N x N matrix A A^H.  Returns (z^(T), c^(T), v^(T), u^(T)) with u^(T) = c^(T) + v^(T-1)
+    the last soft-threshold argument (threshold lam/rho)."""
+    rho = float(rho)
+    G = K.gram_rows()
+    G[np.diag_indices_from(G)] += rho
+    factor = scipy.linalg.cho_factor(G, lower=True)
+
+    def inv(w):
+        return (w - K.adjoint(scipy.linalg.cho_solve(factor, K.forward(w)))) / rho
+
+    d = inv(K.adjoint(y))
+    L = K.shape[1]
+    z = np.zeros(L, np.complex128)
+    v = np.zeros(L, np.complex128)
+    c = z
+    u = z
+    for _ in range(iters):
+        c = d + rho * inv(z - v)
+        u = c + v
+        z_new = soft_threshold(u, lam / rho)
+        v = v + c - z_new
+        z = z_new
+    return z, c, v, u
+
+
 # ------------------------------------------------------------------------------------------
 # Building blocks of Section II-B
 # ------------------------------------------------------------------------------------------
