@@ -222,10 +222,10 @@ def run_reference(args, rank, world):
 # ------------------------------------------------------------------------------------------
 
 
-# ncu capture of fused_solve_kernel<256,256,FISTA,4096> on 38 instances x 20 iterations:
-# dram__bytes_read.sum = 29.96 MB, dram__bytes_write.sum = 2.56 KB
-FUSED_TRAFFIC_TILE = 4096
-FUSED_DRAM_BYTES_PER_INSTANCE = (29.96e6 + 2.56e3) / 38
+# DRAM traffic of the fused kernel per instance, from one ncu capture of a small case of the
+# variant named here (profiles/fused_solve_256x256_fista_ncu_full.md); None until captured
+FUSED_TRAFFIC_VARIANT = None  # (tile, sparse_state)
+FUSED_DRAM_BYTES_PER_INSTANCE = None
 
 
 def load_peaks():
@@ -263,7 +263,7 @@ def run_gpu(args, rank, world, local_rank):
     # untimed preparation: pick the fused kernel's tile per shape class, then capture
     # the whole solve (setup, T iterations, check) with its phase events in one graph
     bccb.bccb_batch_tune(solver.handle, y_dev, 20, args.tune_cache)
-    tile = bccb.bccb_batch_tile(solver.handle, 256, 256)
+    tile, sparse_state = bccb.bccb_batch_variant(solver.handle, 256, 256)
     bccb.bccb_set_timing(solver.handle, True)
     bccb.bccb_batch_capture(solver.handle, y_dev, T, None, c_dev, None, True)
 
@@ -315,54 +315,80 @@ def run_gpu(args, rank, world, local_rank):
     e2e_elapsed = shard.max_over_ranks(time.perf_counter() - t0, device="cuda")
     e2e_value = world * B * T * args.steps / e2e_elapsed
 
-    # ---- iterations (and time) until every sampled instance is within 1e-4 of its
-    # T-iteration result: FISTA's iterates do not depend on T, so a solve with t
-    # iterations gives iterate t of the plain path.
+    # ---- time to 1e-4: iterations until each sampled instance's iterate is within 1e-4 (relative
+    # l2) of the plain path's T-iteration result.  The plain path is the single-instance entry point
+    # (bccb_create + bccb_solve), run with the batch's tile; its result must equal the batched
+    # solve's bit for bit.  FISTA's iterates do not depend on T, so a solve with t iterations gives
+    # iterate t: a scan in steps of 10, then every iteration of the last window, finds each
+    # instance's first t within 1e-4 (errors computed on the device).
     ttt = None
     if rank == 0 and not args.no_ttt:
-        sub = insts[: min(64, B)]
+        n_s = min(64, B)
+        sub = insts[:n_s]
+        gpu_name = torch.cuda.get_device_name(local_rank).replace(" ", "_")
+        with tempfile.NamedTemporaryFile("w", suffix=".txt", delete=False) as f:
+            f.write(f"{gpu_name} 256 256 0 {tile}\n")
+            cache = f.name
+        batched = c_dev.view(-1)[: n_s * 65536].reshape(n_s, 65536).clone()
+        refs, single_ms = [], []
+        for i, d in enumerate(sub):
+            h = bccb.bccb_create(d["M1"], d["M2"], d["mask"], d["L1"], d["L2"], bccb.FISTA, 1.0, stream)
+            y1 = torch.from_numpy(np.asarray(d["y"], np.complex64)).cuda()
+            c1 = torch.empty(65536, dtype=torch.complex64, device="cuda")
+            bccb.bccb_batch_tune(h, y1, 1, cache)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            bccb.bccb_solve(h, y1, d["lam"], True, T, None, c1, check=False)  # warm-up
+            e0.record(stream)
+            bccb.bccb_solve(h, y1, d["lam"], True, T, None, c1, check=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            single_ms.append(e0.elapsed_time(e1))
+            refs.append(c1)
+            bccb.bccb_destroy(h)
+        ref = torch.stack(refs)
+        identical = bool(torch.equal(ref, batched))
+        ref_norm = torch.linalg.vector_norm(ref, dim=1).clamp_min(1e-30)
         sub_solver = bccb.BatchSolver(sub, "fista", stream=stream)
         ys = torch.from_numpy(sub_solver.y_host).cuda()
-        ref = torch.empty(sub_solver.total_c, dtype=torch.complex64, device="cuda")
-        torch.cuda.synchronize()
-        sub_solver.solve(ys, T, ref, check=False)
-        torch.cuda.synchronize()
-        ref_np = sub_solver.unpack(ref.cpu().numpy())
-        cur = torch.empty_like(ref)
-        t_star = None
-        for t in range(10, T + 1, 10):
+        bccb.bccb_batch_tune(sub_solver.handle, ys, 1, cache)
+        cur = torch.empty(n_s * 65536, dtype=torch.complex64, device="cuda")
+
+        def errs(t):
             sub_solver.solve(ys, t, cur, check=False)
-            torch.cuda.synchronize()
-            cur_np = sub_solver.unpack(cur.cpu().numpy())
-            worst = max(float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)) for a, b in zip(cur_np, ref_np))
-            if worst <= 1e-4:
-                t_star = t
+            torch.cuda.synchronize()  # the solve runs on `stream`, the norms on torch's current stream
+            return (torch.linalg.vector_norm(cur.view(n_s, 65536) - ref, dim=1) / ref_norm).cpu().numpy()
+
+        t_star = np.full(n_s, -1)
+        prev = 0
+        for t in list(range(10, T, 10)) + [T]:
+            e = errs(t)
+            hit = (e <= 1e-4) & (t_star < 0)
+            if hit.any():
+                for tt in range(prev + 1, t + 1):  # the first iteration within 1e-4 in (prev, t]
+                    ee = e if tt == t else errs(tt)
+                    new = hit & (ee <= 1e-4) & (t_star < 0)
+                    t_star[new] = tt
+            prev = t
+            if (t_star > 0).all():
                 break
         sub_solver.close()
+        os.unlink(cache)
         per_iter_ms = statistics.median(iterate_ms) / T
-        # the same t_star iterations through the single-instance entry point, one snapshot at a
-        # time (setup, iterations and check of one solve), on the first 8 snapshots
-        single_ms = None
-        if t_star is not None:
-            one_ms = []
-            for d in insts[:8]:
-                one = bccb.BatchSolver([d], "fista", stream=stream)
-                y1 = torch.from_numpy(one.y_host).cuda()
-                c1 = torch.empty(one.total_c, dtype=torch.complex64, device="cuda")
-                one.solve(y1, t_star, c1, check=False)  # warm-up
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                one.solve(y1, t_star, c1, check=False)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                one_ms.append(e0.elapsed_time(e1))
-                one.close()
-            single_ms = statistics.median(one_ms)
-        batched_ms = None if t_star is None else (statistics.median(setup_ms) + t_star * per_iter_ms) / B
-        ttt = {"iters": t_star, "sampled_instances": len(sub), "reference_iters": T,
-               "time_ms_full_batch": None if t_star is None else t_star * per_iter_ms,
-               "batched_ms_per_instance": batched_ms, "single_instance_ms": single_ms,
-               "batched_speedup_vs_single": (single_ms / batched_ms) if (single_ms and batched_ms) else None}
+        t_max = int(t_star.max())
+        # batched: the whole batch's setup and t_max iterations, per instance; plain: each snapshot alone
+        batched_ms = (statistics.median(setup_ms) + t_max * per_iter_ms) / B
+        single_at_t = [ms * ts / T for ms, ts in zip(single_ms, t_star)]
+        ttt = {"plain_path": "single-instance entry point (bccb_create + bccb_solve), same tile as the batch",
+               "plain_equals_batched_bitwise": identical, "sampled_instances": n_s, "reference_iters": T,
+               "t_star": {"min": int(t_star.min()), "median": float(np.median(t_star)), "max": t_max,
+                          "resolution_iters": 1},
+               "time_ms_full_batch": t_max * per_iter_ms,
+               "batched_ms_per_instance": batched_ms,
+               "single_instance_ms_at_t_star": float(statistics.median(single_at_t)),
+               "single_instance_ms_T": float(statistics.median(single_ms)),
+               "batched_speedup_vs_single": float(statistics.median(single_at_t)) / batched_ms,
+               "note": f"the FP64 KKT residual after T = {T} iterations is up to {kkt_max:.2f}: FISTA is far from the "
+                       f"LASSO minimiser on this workload, so its iterates still move near T and t* is close to T"}
 
     if rank == 0:
         peaks = load_peaks()
@@ -375,19 +401,17 @@ def run_gpu(args, rank, world, local_rank):
         achieved = flops_launch / (it_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": None,
-                "kernel": f"fused_solve_kernel<256,256,FISTA,tile={tile}> (one launch per step)",
+                "kernel": f"fused_solve_kernel<256,256,FISTA,tile={tile}"
+                          f"{',sparse state' if sparse_state else ''}> (one launch per step)",
                 "peak_note": f"FP32: {sm_count} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_max:.0f} MHz",
                 "frac_at_median_clock": (achieved / (sm_count * FP32_LANES_PER_SM * 2 * clock["sm_mhz"] * 1e6 / 1e12)
                                          if clock.get("sm_mhz") else None)}
         if args.traffic_bytes is not None:
             roof["traffic"] = args.traffic_bytes
-        elif tile == FUSED_TRAFFIC_TILE and T > 0:
-            # DRAM bytes per launch scaled by instances from an ncu capture of this kernel
-            # (38 instances, 20 iterations); the reads (the q and Bt grids, once per launch)
-            # do not depend on the iteration count
+        elif FUSED_TRAFFIC_VARIANT == (tile, sparse_state) and T > 0:
+            # DRAM bytes per launch scaled by instances from an ncu capture of this kernel variant
             roof["traffic"] = FUSED_DRAM_BYTES_PER_INSTANCE * B
-            roof["traffic_note"] = ("ncu small-case capture scaled by instances; the 512 KB result per instance "
-                                    "stayed in L2 there and is not counted")
+            roof["traffic_note"] = "ncu small-case capture of the same variant, scaled by instances"
         cpu = None
         if not args.no_cpu:
             n_cpu, it_cpu = 2, 300
@@ -406,7 +430,8 @@ def run_gpu(args, rank, world, local_rank):
             "warmup": max(3, args.warmup), "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_name(B, T), "batch_per_gpu": B, "L1": 256, "L2": 256, "iters": T,
-                       "tile": tile, "launch": "CUDA graph of the whole solve, replayed per step",
+                       "tile": tile, "sparse_state": bool(sparse_state),
+                       "launch": "CUDA graph of the whole solve, replayed per step",
                        "l2_policy": f"inputs larger than L2: {solver.total_c * 8 * 7 / 2**30:.1f} GiB resident per GPU",
                        "parallelism": f"instances sharded over {world} GPU(s)"},
             "phases_ms": {"setup": statistics.mean(setup_ms), "iterate": it_ms, "check": statistics.mean(check_ms)},
@@ -474,11 +499,23 @@ def run_workload(args):
                  for s in snaps]
         _, t, _ = _solve_timed(bccb, torch, insts, "fista", T, check=True)
         elems = sum(s.L1 * s.L2 for s in snaps)
+        # A/B: the same instances, each (L1, L2) class solved on its own (its own solver and launch,
+        # one after another), against the one call above whose class launches run concurrently
+        classes = {}
+        for d in insts:
+            classes.setdefault((d["L1"], d["L2"]), []).append(d)
+        solo = {}
+        for key, group in sorted(classes.items()):
+            _, tk, _ = _solve_timed(bccb, torch, group, "fista", T, check=False)
+            solo[f"{key[0]}x{key[1]}"] = {"instances": len(group), "iterate_ms": tk["iterate_ms"]}
+        seq_ms = sum(v["iterate_ms"] for v in solo.values())
         line = {"workload": f"ragged FISTA batch: {B} snapshots, L1,L2 uniform on {{64,128,256}}, M_i = L_i/4, "
                             f"25% occupancy, K in 1..10, SNR 0..30 dB, {T} iterations",
                 "value": B * T / (t["ms"] / 1e3), "unit": "instance-iterations/s", "phases_ms": t,
                 "grid_elements": elems, "flop_rate_tflops": sum(flops_per_inst_iter(s.L1, s.L2) for s in snaps)
-                * T / (t["iterate_ms"] / 1e3) / 1e12}
+                * T / (t["iterate_ms"] / 1e3) / 1e12,
+                "ab_classes": {"concurrent_iterate_ms": t["iterate_ms"], "one_class_at_a_time_iterate_ms": seq_ms,
+                               "per_class": solo}}
     elif args.workload == "precision1024":
         # the precision study at full length: FP32 and FP64 GPU paths, ADMM x 2000 at the stated rho = 0.5
         # and at rho = N = 1024, each result's error against the stored FP64 oracle reference
@@ -507,6 +544,111 @@ def run_workload(args):
                 "reference": "FP64 oracle (tests/golden/admm1024_rho*.txt): z^(T) in full, c^(T) on 1024 sampled "
                              "entries and in norm",
                 "studies": studies}
+    elif args.workload == "learned":
+        # unrolled FISTA, 16 layers with learned per-layer step and threshold multipliers (fixed 32x32
+        # array, N = 256, 256x256 grid), judged against 1000-iteration plain FISTA
+        from paper_2509_13592_gb300 import learned as Lm
+
+        cfg = Lm.TrainConfig()
+        path = args.params or os.path.join(ROOT, "paper_2509_13592_gb300", "unrolled_fista16_256.json")
+        if os.path.exists(path):
+            with open(path) as f:
+                p = json.load(f)
+            scale = torch.tensor(p["scale"], dtype=torch.float32, device="cuda")
+            thresh = torch.tensor(p["thresh"], dtype=torch.float32, device="cuda")
+            trained = {"file": os.path.relpath(path, ROOT), "snapshots": p["train_snapshots"]}
+        else:  # no stored multipliers: a short training run here
+            cfg.steps = 100
+            scale, thresh, hist = Lm.train(cfg, log=None)
+            trained = {"file": None, "snapshots": cfg.steps * cfg.batch, "loss_last": hist[-1]}
+        n_eval, T = 8192, cfg.target_iters
+        mask = Lm.fixed_mask(cfg)
+        y = Lm.snapshot_batch(cfg, mask, 10**7, n_eval)
+        L = cfg.L1 * cfg.L2
+        one = dict(M1=cfg.M1, M2=cfg.M2, L1=cfg.L1, L2=cfg.L2, mask=mask, y=np.zeros(cfg.N, np.complex64),
+                   lam=cfg.lam_frac, lam_is_frac=True)
+        stream = torch.cuda.Stream()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+        def timed(fn):
+            torch.cuda.synchronize()
+            ev0.record()
+            out = fn()
+            ev1.record()
+            torch.cuda.synchronize()
+            return out, ev0.elapsed_time(ev1)
+
+        solver = bccb.BatchSolver([one] * n_eval, "fista")
+        bccb.bccb_batch_tune(solver.handle, y, 5, None)
+        ref = torch.empty(n_eval * L, dtype=torch.complex64, device="cuda")
+        solver.solve(y, 10, ref, check=False)  # warm-up
+
+        def plain(iters, yy=y, s=solver, n=n_eval, c0=None):
+            o = torch.empty(n * L, dtype=torch.complex64, device="cuda")
+            s.solve(yy, iters, o, c0=c0, check=False)
+            torch.cuda.synchronize()
+            return o
+
+        ref, t_ref = timed(lambda: plain(T))
+        net = Lm.UnrolledNet(cfg.M1, cfg.M2, mask, cfg.L1, cfg.L2, n_eval, cfg.lam_frac)
+        with torch.no_grad():
+            Lm.net_forward(net, y, scale, thresh)  # warm-up
+            c_net, t_net = timed(lambda: Lm.net_forward(net, y, scale, thresh))
+        e_net = Lm.relative_errors(c_net, ref, n_eval, L)
+        sweep = {}
+        for it in (16, 32, 48, 64):
+            o, t = timed(lambda: plain(it))
+            e = Lm.relative_errors(o, ref, n_eval, L)
+            sweep[it] = {"ms": t, "rel_err_mean": e.mean().item()}
+        net.close()
+        # time to 1e-4 of the target on a 64-snapshot sample: plain FISTA from zero, and the network
+        # followed by plain FISTA warm-started from its output (momentum restarted), the fallback path
+        n_s = 64
+        ys = y[: n_s * cfg.N].contiguous()
+        refs = ref[: n_s * L].view(n_s, L)
+        rn = torch.linalg.vector_norm(refs, dim=1)
+        sub = bccb.BatchSolver([one] * n_s, "fista")
+
+        def worst(o):
+            return float((torch.linalg.vector_norm(o.view(n_s, L) - refs, dim=1) / rn).max())
+
+        t_plain = next((t for t in range(10, T + 1, 10) if worst(plain(t, ys, sub, n_s)) <= 1e-4), None)
+        if t_plain is not None:
+            t_plain = next(t for t in range(t_plain - 9, t_plain + 1) if worst(plain(t, ys, sub, n_s)) <= 1e-4)
+        c_sub = c_net[: n_s * L].contiguous()
+        fb = {k: worst(plain(k, ys, sub, n_s, c0=c_sub)) for k in (1, 10, 100, 250, 500, 1000, 2000)}
+        k_hit = next((k for k, w in fb.items() if w <= 1e-4), None)
+        sub.close()
+        per_it = t_ref / T / n_eval
+        # plain single-instance FISTA (bccb_create + bccb_solve), T iterations, first 8 snapshots
+        single = []
+        for i in range(8):
+            h = bccb.bccb_create(cfg.M1, cfg.M2, mask, cfg.L1, cfg.L2, bccb.FISTA, 1.0, stream)
+            y1 = y[i * cfg.N:(i + 1) * cfg.N].contiguous()
+            c1 = torch.empty(L, dtype=torch.complex64, device="cuda")
+            bccb.bccb_solve(h, y1, cfg.lam_frac, True, T, None, c1, check=False)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            bccb.bccb_solve(h, y1, cfg.lam_frac, True, T, None, c1, check=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            single.append(e0.elapsed_time(e1))
+            bccb.bccb_destroy(h)
+        solver.close()
+        line = {"workload": f"unrolled FISTA: 16 layers with learned per-layer step and threshold multipliers, fixed "
+                            f"32x32 array N=256, 256x256 grid, K in 1..8 off-grid, SNR 0..30 dB, lam=0.05||A^H y||_inf; "
+                            f"inference on {n_eval} snapshots; judge: {T}-iteration plain FISTA",
+                "trained": trained,
+                "target_batched_ms": t_ref, "net_ms": t_net,
+                "net_rel_err_mean": e_net.mean().item(), "net_rel_err_median": e_net.median().item(),
+                "plain_batched": sweep,
+                "time_to_1e-4_of_target": {
+                    "sample": n_s, "plain_batched_iters": t_plain,
+                    "plain_batched_ms_per_instance": None if t_plain is None else t_plain * per_it,
+                    "plain_single_instance_ms": statistics.median(single) * (t_plain or T) / T,
+                    "net_then_fallback_worst_rel_err_after_k_iters": fb, "net_then_fallback_iters": k_hit,
+                    "net_then_fallback_ms_per_instance": None if k_hit is None else t_net / n_eval + k_hit * per_it}}
     elif args.workload == "peaks":
         # harmonic / angle extraction (Section II-A) on the solutions of the batched 256x256 workload
         B, T, K = args.batch, args.iters, 16
@@ -659,9 +801,11 @@ def main():
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-1e-4 measurement")
     ap.add_argument("--tune-cache", default=None, help="autotuner cache file (default: measure every run)")
     ap.add_argument("--workload", default="batched256",
-                    choices=["batched256", "ragged", "precision1024", "single64", "table1", "peaks", "toeplitz"],
+                    choices=["batched256", "ragged", "precision1024", "single64", "table1", "peaks", "toeplitz",
+                             "learned"],
                     help="batched256 is the benchmark metric; the others print their own line")
     ap.add_argument("--trials", type=int, default=3, help="trials per Table I cell (--workload table1)")
+    ap.add_argument("--params", default=None, help="trained multipliers of the unrolled network (--workload learned)")
     ap.add_argument("--traffic-bytes", type=float, default=None,
                     help="DRAM bytes per launch of the fused kernel from an ncu capture")
     args = ap.parse_args()

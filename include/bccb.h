@@ -189,14 +189,19 @@ int bccb_batch_capture(bccb_solver_t s, const void* y_dev, int iters, const void
                        void* aux_out_dev, int check);
 int bccb_batch_replay(bccb_solver_t s);
 
-/* Autotuner: for every (L1, L2) class of the batch, time each fused-kernel tile
+/* Autotuner: for every (L1, L2) class of the batch, time each fused-kernel variant
  * (8192 grid elements per CTA, or 4096 = twice the CTAs per cluster, two CTAs per
+ * SM, both with the state in shared memory; for ISTA/FISTA on rows of 256 also 8192
+ * elements per CTA with the state held only at its nonzero positions, two CTAs per
  * SM) for probe_iters iterations on the class's own instances, after one setup with
  * y_dev, and keep the fastest.  cache_path (nullable): a text file of lines
- * "gpu_name L1 L2 admm tile"; classes found there for this GPU are not measured,
- * new choices are appended.  Synchronises.  bccb_batch_tile reports the choice. */
+ * "gpu_name L1 L2 admm tile sparse" (a line without the last field means sparse = 0);
+ * classes found there for this GPU are not measured, new choices are appended.
+ * Synchronises.  bccb_batch_tile reports the tile and bccb_batch_variant the tile
+ * and whether the state is sparse (0 for a multi-pass class). */
 int bccb_batch_tune(bccb_solver_t s, const void* y_dev, int probe_iters, const char* cache_path);
 int bccb_batch_tile(bccb_solver_t s, int L1, int L2, int* tile);
+int bccb_batch_variant(bccb_solver_t s, int L1, int L2, int* tile, int* sparse_state);
 
 /* Unrolled FISTA network (a learned extension of eq:fista; the paper has no learned
  * part).  On a FISTA solver, layer k = 0..layers-1 runs

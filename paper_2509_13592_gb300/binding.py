@@ -65,6 +65,7 @@ def _load():
     lib.bccb_batch_replay.argtypes = [vp]
     lib.bccb_batch_tune.argtypes = [vp, vp, i32, ctypes.c_char_p]
     lib.bccb_batch_tile.argtypes = [vp, i32, i32, P(i32)]
+    lib.bccb_batch_variant.argtypes = [vp, i32, i32, P(i32), P(i32)]
     lib.bccb_unrolled_fwd.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, i32]
     lib.bccb_unrolled_bwd.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp]
     lib.bccb_batch_peaks.argtypes = [vp, vp, i32, dbl, vp, vp, vp, vp, vp]
@@ -80,7 +81,7 @@ def _load():
                  "bccb_batch_get", "bccb_create", "bccb_solve", "bccb_batch_size", "bccb_instance_shape",
                  "bccb_destroy", "bccb_set_timing", "bccb_last_timing", "bccb_batch_capture", "bccb_batch_replay",
                  "bccb_batch_tune", "bccb_batch_tile", "bccb_unrolled_fwd", "bccb_unrolled_bwd", "bccb_batch_peaks",
-                 "bccb_batch_set_method", "bccb_batch_create_gamma", "bccb_set_kkt_tol", "bccb_mu", "bccb_batch_status"):
+                 "bccb_batch_set_method", "bccb_batch_create_gamma", "bccb_set_kkt_tol", "bccb_mu", "bccb_batch_status", "bccb_batch_variant"):
         getattr(lib, name).restype = i32
     return lib
 
@@ -226,6 +227,13 @@ def bccb_batch_tile(h: int, L1: int, L2: int) -> int:
     t = ctypes.c_int(0)
     _raise(_lib.bccb_batch_tile(h, int(L1), int(L2), ctypes.byref(t)), h)
     return t.value
+
+
+def bccb_batch_variant(h: int, L1: int, L2: int):
+    """(tile, sparse_state) of the fused kernel chosen for the (L1, L2) class."""
+    t, sp = ctypes.c_int(0), ctypes.c_int(0)
+    _raise(_lib.bccb_batch_variant(h, int(L1), int(L2), ctypes.byref(t), ctypes.byref(sp)), h)
+    return t.value, sp.value
 
 
 def bccb_unrolled_fwd(h: int, y_dev, batch: int, layers: int, scale_dev, thresh_dev, c_out_dev, saved_dev=None,

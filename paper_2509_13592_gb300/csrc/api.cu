@@ -99,7 +99,7 @@ void release(bccb_solver* s) {
                   s->d_kkt,    s->d_obj,      s->d_red,     s->d_tw32,    s->d_tw64,    s->d_y_stage,
                   s->d_c_stage, s->d_mult64,  s->d_bt64,    s->d_mp_work, s->d_mp_s0,   s->d_mp_s1,
                   s->d_cint,   s->d_c0int,    s->d_toep_h,  s->d_toep_fb, s->d_lam_sel, s->d_lam_src,
-                  s->d_lo};
+                  s->d_lo,     s->d_hi};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -318,15 +318,18 @@ int create_impl(bccb_solver_t* out, const bccb_inst_t* insts, int n, const uint8
     CREATE_CUDA(bccb::prepare_multipass(s));
   }
   CREATE_CUDA(bccb::fill_twiddles(s));
-  bool any_fused = false;
+  bool any_fused = false, any_sparse = false;
   for (auto& c : s->classes)
     if (!c.multipass) {
       CREATE_CUDA(c.entry.prepare());
       any_fused = true;
+      any_sparse = any_sparse || (algo != BCCB_ADMM && !blk && bccb::fused_lookup(c.L1, c.L2, false, 0, false, true));
     }
   // the fused ISTA/FISTA kernel keeps the low-order parts of its state here (8 bytes per cell;
-  // only cells where the state is nonzero are ever read or written, so no initialisation)
+  // only cells where the state is nonzero are ever read or written, so no initialisation), and
+  // its sparse-state variant the high parts of the positions its slots cannot hold (16 bytes)
   if (any_fused && algo != BCCB_ADMM) CREATE_CUDA(dalloc(&s->d_lo, s->total_c));
+  if (any_sparse) CREATE_CUDA(dalloc(&s->d_hi, s->total_c));
   if (s->classes.size() > 1) {
     CREATE_CUDA(cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming));
     for (size_t k = 0; k < s->classes.size(); ++k) {
@@ -444,6 +447,7 @@ int solve_impl(bccb_solver_t s, const void* y_dev, int iters, const void* c0_dev
   a.c_out = reinterpret_cast<float2*>(k_out);
   a.aux_out = (s->algo == BCCB_ADMM) ? reinterpret_cast<float2*>(aux_out_dev) : nullptr;
   a.lo = s->d_lo;
+  a.hi = s->d_hi;
   a.iters = iters;
   a.pad_ = 0;
   if (s->method == BCCB_DENSE) {
@@ -791,14 +795,16 @@ int bccb_batch_tune(bccb_solver_t s, const void* y_dev, int probe_iters, const c
   std::string gpu(prop.name);
   for (char& ch : gpu)
     if (ch == ' ') ch = '_';
-  // cached choices: lines "gpu L1 L2 admm tile"
-  std::map<std::tuple<int, int, int>, int> cached;
+  // cached choices: lines "gpu L1 L2 admm tile [sparse]" (a missing last field reads as 0)
+  std::map<std::tuple<int, int, int>, std::pair<int, int>> cached;
   if (cache_path) {
     if (FILE* f = fopen(cache_path, "r")) {
-      char name[256];
-      int l1, l2, ad, tile;
-      while (fscanf(f, "%255s %d %d %d %d", name, &l1, &l2, &ad, &tile) == 5)
-        if (gpu == name) cached[std::make_tuple(l1, l2, ad)] = tile;
+      char line[512], name[256];
+      while (fgets(line, sizeof line, f)) {
+        int l1, l2, ad, tile, sparse = 0;
+        const int got = sscanf(line, "%255s %d %d %d %d %d", name, &l1, &l2, &ad, &tile, &sparse);
+        if (got >= 5 && gpu == name) cached[std::make_tuple(l1, l2, ad)] = {tile, got == 6 ? sparse : 0};
+      }
       fclose(f);
     }
   }
@@ -827,8 +833,9 @@ int bccb_batch_tune(bccb_solver_t s, const void* y_dev, int probe_iters, const c
     const auto key = std::make_tuple(c.entry.L1, c.entry.L2, admm);
     auto it = cached.find(key);
     if (it != cached.end()) {
+      const bool sp = it->second.second != 0 && s->d_hi != nullptr;
       if (const bccb::FusedEntry* fe =
-              bccb::fused_lookup(c.entry.L1, c.entry.L2, admm != 0, it->second, s->toeplitz != 0)) {
+              bccb::fused_lookup(c.entry.L1, c.entry.L2, admm != 0, it->second.first, s->toeplitz != 0, sp)) {
         c.entry = *fe;
         if (c.entry.prepare() != cudaSuccess) status = BCCB_ERR_CUDA;
         continue;
@@ -845,12 +852,19 @@ int bccb_batch_tune(bccb_solver_t s, const void* y_dev, int probe_iters, const c
     a.c_out = s->d_probe;
     a.aux_out = nullptr;
     a.lo = s->d_lo;
+    a.hi = s->d_hi;
     a.iters = probe_iters;
     a.pad_ = 0;
     float best = 1e30f;
     bccb::FusedEntry best_e = c.entry;
-    for (int tile : {8192, 4096}) {
-      const bccb::FusedEntry* fe = bccb::fused_lookup(c.entry.L1, c.entry.L2, admm != 0, tile, s->toeplitz != 0);
+    // candidates: the 8192- and 4096-element tiles with the state in shared memory, and the
+    // 8192-element tile with the sparse state (where it exists and its arrays were allocated)
+    const std::pair<int, int> cands[] = {{8192, 0}, {4096, 0}, {8192, 1}};
+    for (const auto& cand : cands) {
+      const int tile = cand.first;
+      if (cand.second && !s->d_hi) continue;
+      const bccb::FusedEntry* fe =
+          bccb::fused_lookup(c.entry.L1, c.entry.L2, admm != 0, tile, s->toeplitz != 0, cand.second != 0);
       if (!fe || fe->prepare() != cudaSuccess) continue;
       float ms = 0.f;
       bool ok = fe->launch(a, c.count, s->stream) == cudaSuccess;  // warm-up
@@ -865,7 +879,8 @@ int bccb_batch_tune(bccb_solver_t s, const void* y_dev, int probe_iters, const c
       }
     }
     c.entry = best_e;
-    if (out) fprintf(out, "%s %d %d %d %d\n", gpu.c_str(), c.entry.L1, c.entry.L2, admm, c.entry.tile);
+    if (out)
+      fprintf(out, "%s %d %d %d %d %d\n", gpu.c_str(), c.entry.L1, c.entry.L2, admm, c.entry.tile, c.entry.sparse);
   }
   if (out) fclose(out);
   if (e0) cudaEventDestroy(e0);
@@ -996,10 +1011,18 @@ int bccb_batch_peaks(bccb_solver_t s, const void* c_dev, int K, double rel_thres
 }
 
 int bccb_batch_tile(bccb_solver_t s, int L1, int L2, int* tile) {
+  return bccb_batch_variant(s, L1, L2, tile, nullptr);
+}
+
+int bccb_batch_variant(bccb_solver_t s, int L1, int L2, int* tile, int* sparse_state) {
   if (!s || !tile) return fail(s, BCCB_ERR_INVALID_ARG, "NULL argument");
   *tile = 0;
+  if (sparse_state) *sparse_state = 0;
   for (const auto& c : s->classes)
-    if (c.L1 == L1 && c.L2 == L2) *tile = c.multipass ? 0 : c.entry.tile;
+    if (c.L1 == L1 && c.L2 == L2) {
+      *tile = c.multipass ? 0 : c.entry.tile;
+      if (sparse_state) *sparse_state = c.multipass ? 0 : c.entry.sparse;
+    }
   return BCCB_OK;
 }
 

@@ -3,11 +3,11 @@
 
 namespace bccb {
 
-const FusedEntry* fused_lookup_L2_16(int L1, bool admm, int tile, bool block);
-const FusedEntry* fused_lookup_L2_32(int L1, bool admm, int tile, bool block);
-const FusedEntry* fused_lookup_L2_64(int L1, bool admm, int tile, bool block);
-const FusedEntry* fused_lookup_L2_128(int L1, bool admm, int tile, bool block);
-const FusedEntry* fused_lookup_L2_256(int L1, bool admm, int tile, bool block);
+const FusedEntry* fused_lookup_L2_16(int L1, bool admm, int tile, bool block, bool sparse);
+const FusedEntry* fused_lookup_L2_32(int L1, bool admm, int tile, bool block, bool sparse);
+const FusedEntry* fused_lookup_L2_64(int L1, bool admm, int tile, bool block, bool sparse);
+const FusedEntry* fused_lookup_L2_128(int L1, bool admm, int tile, bool block, bool sparse);
+const FusedEntry* fused_lookup_L2_256(int L1, bool admm, int tile, bool block, bool sparse);
 
 const AdjointEntry* adjoint_lookup_L2_16(int L1);
 const AdjointEntry* adjoint_lookup_L2_32(int L1);
@@ -43,14 +43,14 @@ const AdjointEntry* adjoint_lookup(int L1, int L2) {
   }
 }
 
-const FusedEntry* fused_lookup(int L1, int L2, bool admm, int tile, bool block) {
+const FusedEntry* fused_lookup(int L1, int L2, bool admm, int tile, bool block, bool sparse) {
   if (tile == 0) tile = kFusedTileElems;
   switch (L2) {
-    case 16: return fused_lookup_L2_16(L1, admm, tile, block);
-    case 32: return fused_lookup_L2_32(L1, admm, tile, block);
-    case 64: return fused_lookup_L2_64(L1, admm, tile, block);
-    case 128: return fused_lookup_L2_128(L1, admm, tile, block);
-    case 256: return fused_lookup_L2_256(L1, admm, tile, block);
+    case 16: return fused_lookup_L2_16(L1, admm, tile, block, sparse);
+    case 32: return fused_lookup_L2_32(L1, admm, tile, block, sparse);
+    case 64: return fused_lookup_L2_64(L1, admm, tile, block, sparse);
+    case 128: return fused_lookup_L2_128(L1, admm, tile, block, sparse);
+    case 256: return fused_lookup_L2_256(L1, admm, tile, block, sparse);
     default: return nullptr;
   }
 }

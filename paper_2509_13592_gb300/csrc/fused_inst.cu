@@ -22,7 +22,11 @@ namespace bccb {
 #define BCCB_BLOCK(L1) fused_entry<L1, BCCB_L2, false, kFusedTileElems, false, true>()
 #define BCCB_BLOCK_HALF(L1) fused_entry<L1, BCCB_L2, false, 4096, false, true>()
 
-const FusedEntry* BCCB_CAT(fused_lookup_L2_, BCCB_L2)(int L1, bool admm, int tile, bool block) {
+// ISTA/FISTA with the state outside shared memory: rows of 256, 8192 elements per CTA, two CTAs
+// per SM (needs at least 32 rows)
+#define BCCB_SPARSE(L1) fused_entry<L1, BCCB_L2, false, kFusedTileElems, false, false, true>()
+
+const FusedEntry* BCCB_CAT(fused_lookup_L2_, BCCB_L2)(int L1, bool admm, int tile, bool block, bool sparse) {
   static const FusedEntry table[] = {
       BCCB_ENTRIES(16), BCCB_ENTRIES(32), BCCB_ENTRIES(64), BCCB_ENTRIES(128), BCCB_ENTRIES(256),
 #if BCCB_L2 >= 32
@@ -49,9 +53,14 @@ const FusedEntry* BCCB_CAT(fused_lookup_L2_, BCCB_L2)(int L1, bool admm, int til
 #if BCCB_L2 >= 256
       BCCB_BLOCK_HALF(32),
 #endif
+#if BCCB_L2 >= 32
+      BCCB_SPARSE(256),
+#endif
   };
   for (const FusedEntry& e : table)
-    if (e.L1 == L1 && e.admm == (admm ? 1 : 0) && e.tile == tile && e.block == (block ? 1 : 0)) return &e;
+    if (e.L1 == L1 && e.admm == (admm ? 1 : 0) && e.tile == tile && e.block == (block ? 1 : 0) &&
+        e.sparse == (sparse ? 1 : 0))
+      return &e;
   return nullptr;
 }
 

@@ -73,6 +73,8 @@ struct FusedArgs {
   // ISTA/FISTA: low-order parts of the state, packed like c_out: {c_lo, z_lo} as bf16 pairs.
   // Read and written only where the state is nonzero (see the update in fused_solve_kernel).
   uint2* lo;
+  // sparse-state variant: high parts {c_hi, z_hi} of the positions its slots cannot hold
+  float4* hi;
   int iters;
   int pad_;
 };
@@ -117,15 +119,19 @@ __host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
 // 4096-element tile doubles the cluster and fits two CTAs per SM.
 constexpr int kFusedTileElems = 8192;
 
-template <int L1_, int L2_, bool ADMM_, int TILE_ = kFusedTileElems>
+// SPARSE: the ISTA/FISTA state is not kept as two dense grids in shared memory but only at its
+// nonzero positions (per-thread slots, global memory beyond them), and each thread runs the row
+// stages over two bands of rows; 8192 elements then fit in ~106 KB and two CTAs share an SM.
+template <int L1_, int L2_, bool ADMM_, int TILE_ = kFusedTileElems, bool SPARSE_ = false>
 struct FusedShape {
   static constexpr int L1 = L1_, L2 = L2_, TILE = TILE_;
-  static constexpr bool ADMM = ADMM_;
+  static constexpr bool ADMM = ADMM_, SPARSE = SPARSE_;
+  static constexpr int PASSES = SPARSE ? 2 : 1;                  // row bands per thread
   static constexpr int C = cmax(1, (L1 * L2) / TILE);  // CTAs per cluster
   static constexpr int R = L2 / C;                                // rows per CTA
   static constexpr int E = R * L1;                                // elements per CTA
-  static constexpr int T = cmax(32, E / 16);                      // threads per CTA
-  static constexpr int V = E / T;                                 // elements per thread per stage
+  static constexpr int T = cmax(32, E / (16 * PASSES));           // threads per CTA
+  static constexpr int V = E / T / PASSES;                        // elements per thread per stage and band
   static constexpr int Q = cmin(16, L2);                          // cross-group radix
   static constexpr int QV = Q / C;                                // groups per CTA
   static constexpr int RP = L2 / Q;                               // local column DFT length
@@ -147,11 +153,16 @@ struct FusedShape {
   static constexpr int POFF = SPLIT_MID ? ((SH * 2 + 15) / 16) * 16 : 0;
   // work (padded) + two state grids + twiddles + a frequency bit mask per middle-stage pair
   // + W_256^{i j} (16 x 16, rows of 256) + W_16^m + the cached multipliers and offsets
+  // rows per band of the SQ16 row stages: two rows per warp
+  static constexpr int BAND = 2 * (T / 32);
   // ISTA/FISTA: two 8-byte slots per thread for the low-order parts of its first two
-  // positions with a nonzero state (see the update in fused_solve_kernel)
-  static constexpr int SLOTS = ADMM ? 0 : 2 * T * 8;
-  static constexpr int SMEM = (R * P + 2 * E) * 8 + NMAX * 8 + ((SH * 2 + 15) / 16) * 16 + 256 * 8 + 16 * 8 +
+  // positions with a nonzero state (see the update in fused_solve_kernel); the sparse variant
+  // keeps {c_hi, z_hi} and the low parts there (24 bytes), in two sets used alternately
+  static constexpr int SLOTS = ADMM ? 0 : SPARSE ? 2 * 2 * T * 24 : 2 * T * 8;
+  static constexpr int STATE = SPARSE ? 0 : 2 * E * 8;          // dense state grids
+  static constexpr int SMEM = R * P * 8 + STATE + NMAX * 8 + ((SH * 2 + 15) / 16) * 16 + 256 * 8 + 16 * 8 +
                               MCAP * 16 + POFF + SLOTS;
+  static_assert(!SPARSE || (SQ16 && !ADMM && PASSES * BAND == R), "sparse state: rows of 256, ISTA/FISTA");
   static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
   static_assert((R * P * 8) % 16 == 0, "16-byte aligned layout after the work rows");
   // two CTAs per SM when their shared memory fits (227 KB per CTA, 228 KB per SM)
@@ -228,6 +239,7 @@ struct FusedCta {
   uint16_t* poff;   // per active pair: index of its first entry in mtab
   int crank;
   int tid;
+  int band = 0;  // SQ16 row stages: the band of S::BAND rows being processed
   // every nonzero frequency of this CTA's pairs has q < 2 (the spectrum lives in the first
   // 2 RP rows, e.g. a 32-row array on a 256-row grid): the split middle stage then forms
   // and reads only X[0] and X[1] of each 16-point butterfly
@@ -355,7 +367,7 @@ struct FusedCta {
   // stage reads just its first nz inputs.
   // ---------------------------------------------------------------------------------------
   __device__ __forceinline__ void sq_rowj(int& row, int& j) const {
-    row = (tid >> 5) * 2 + ((tid & 31) >> 4);
+    row = band * S::BAND + (tid >> 5) * 2 + ((tid & 31) >> 4);
     j = tid & 15;
   }
   // with j < 16, the padded position of j + 16 i is j + 17 i and that of 16 j + k is 17 j + k:
@@ -523,7 +535,7 @@ struct FusedCta {
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
       bool f;
-      v[i] = quick(row, j + 16 * i, i, v[i], f);
+      v[i] = quick(row, j + 16 * i, 16 * band + i, v[i], f);
       if (f) flagged |= 1u << i;
     }
     if (flagged) {
@@ -533,7 +545,7 @@ struct FusedCta {
 #pragma unroll 1
       for (uint32_t m = flagged; m; m &= m - 1u) {
         const int i = __ffs(m) - 1;
-        bp[i] = ext(row, j + 16 * i, i, bp[i]);
+        bp[i] = ext(row, j + 16 * i, 16 * band + i, bp[i]);
       }
 #pragma unroll
       for (int i = 0; i < 16; ++i)
@@ -914,21 +926,23 @@ __device__ __forceinline__ void cluster_barrier() {
 // plain solves are compiled without them.
 // BLOCK: the grid is the circulant embedding of a Toeplitz Gram and the update keeps the
 // unknown at 0 outside the instance's block (FusedInst::bl1, bl2); ordinary grids compile without it.
-template <int L1, int L2, bool ADMM, int TILE, bool LEARN = false, bool BLOCK = false>
-__global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<L1, L2, ADMM, TILE>::MIN_BLOCKS)
+// SPARSE: the state outside shared memory (see FusedShape); ISTA/FISTA solves only.
+template <int L1, int L2, bool ADMM, int TILE, bool LEARN = false, bool BLOCK = false, bool SPARSE = false>
+__global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE, SPARSE>::T,
+                                  FusedShape<L1, L2, ADMM, TILE, SPARSE>::MIN_BLOCKS)
     fused_solve_kernel(const FusedArgs a) {
-  using S = FusedShape<L1, L2, ADMM, TILE>;
+  using S = FusedShape<L1, L2, ADMM, TILE, SPARSE>;
   constexpr int C = S::C, E = S::E, T = S::T, P = S::P, NMAX = S::NMAX, R = S::R;
+  static_assert(!SPARSE || (!LEARN && !BLOCK), "the sparse-state variant serves plain solves");
 
   extern __shared__ float4 smem_raw[];
   FusedCta<S> cta;
   char* sp = reinterpret_cast<char*>(smem_raw);
   cta.work = reinterpret_cast<float2*>(sp);
   sp += R * P * 8;
-  cta.s0 = reinterpret_cast<float2*>(sp);
-  sp += E * 8;
-  cta.s1 = reinterpret_cast<float2*>(sp);
-  sp += E * 8;
+  cta.s0 = SPARSE ? nullptr : reinterpret_cast<float2*>(sp);
+  cta.s1 = SPARSE ? nullptr : reinterpret_cast<float2*>(sp + E * 8);
+  sp += S::STATE;
   cta.tw = reinterpret_cast<float2*>(sp);
   sp += NMAX * 8;
   cta.pmask = reinterpret_cast<uint16_t*>(sp);
@@ -942,6 +956,9 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
   cta.poff = reinterpret_cast<uint16_t*>(sp);
   sp += S::POFF;
   uint2* const slot = reinterpret_cast<uint2*>(sp) + 2 * threadIdx.x;  // this thread's two slots
+  // sparse variant: slot sets [2][2][T] of {c_hi, z_hi} (float4) and of the low parts (uint2)
+  float4* const shi = reinterpret_cast<float4*>(sp);
+  uint2* const slo = reinterpret_cast<uint2*>(sp + 2 * 2 * T * 16);
   cta.tid = threadIdx.x;
   int crank = 0;
   if constexpr (C > 1) crank = (int)cg::this_cluster().block_rank();
@@ -969,12 +986,15 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
   // ---- load twiddles, the frequency masks and the initial state
   cta.load_tables(a.twiddle, mult, bt, kc);
   uint2* const lo = ADMM ? nullptr : a.lo + in.c_off;
+  float4* const hi = SPARSE ? a.hi + in.c_off : nullptr;
   for (int idx = threadIdx.x; idx < E; idx += T) {
     const int s = idx / L1, e = idx % L1;
     const int gidx = (crank + C * s) * L1 + e;
     float2 x = c0 ? c0[gidx] : make_float2(0.f, 0.f);
-    cta.s0[idx] = x;                                 // c^(0) or z^(0)
-    cta.s1[idx] = ADMM ? make_float2(0.f, 0.f) : x;  // z^(1) = c^(0), or v^(0) = 0
+    if constexpr (!SPARSE) {
+      cta.s0[idx] = x;                                 // c^(0) or z^(0)
+      cta.s1[idx] = ADMM ? make_float2(0.f, 0.f) : x;  // z^(1) = c^(0), or v^(0) = 0
+    }
     cta.work[s * P + pad16(e)] = x;
   }
   __syncthreads();
@@ -985,15 +1005,21 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
   // sit in the thread's two shared-memory slots, those of any further ones in global memory (lo,
   // packed like c_out).  The first epilogue treats every position as live with a zero low-order
   // part (a complex64 warm start is exact), so no memory has to be cleared beforehand.
+  // The sparse variant keeps the whole state of a live position, {c_hi, z_hi} and the low parts,
+  // in the thread's two slots of the current set (global memory, hi and lo, for any further ones)
+  // and writes the new state to the other set, so the sets alternate between iterations; the
+  // first epilogue reads the warm start itself.
   uint32_t live = 0xffffffffu, live_next = 0u;
-  int ord = 0, rank_old = 0, rank_new = 0;
+  int ord = 0, rank_old = 0, rank_new = 0, set = 0;
   uint2 slot_old0 = make_uint2(0u, 0u), slot_old1 = make_uint2(0u, 0u);
   bool first = true;
   auto epilogue_begin = [&]() {
     if constexpr (!ADMM) {
-      if (!first) {
-        slot_old0 = slot[0];
-        slot_old1 = slot[1];
+      if constexpr (!SPARSE) {
+        if (!first) {
+          slot_old0 = slot[0];
+          slot_old1 = slot[1];
+        }
       }
       ord = rank_old = rank_new = 0;
       live_next = 0u;
@@ -1003,6 +1029,7 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
     if constexpr (!ADMM) {
       live = live_next;
       first = false;
+      set ^= 1;
     }
   };
 
@@ -1020,7 +1047,8 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
   // quick: every output of the inverse transform (the thread's o-th).  Off the support the
   // state is exactly 0 and stays 0 while |G'| <= kappa: that element is finished here, touching
   // no memory.  Otherwise it is flagged and the (scaled) G' is kept for ext.
-  auto quick = [&](int row, int e, int o, float2 g, bool& flag, float sc, float kap, float2* save_t) -> float2 {
+  auto quick = [&](int row, int e, int o, float2 g, bool& flag, float sc, float kap, float2* save_t,
+                   bool last) -> float2 {
     if constexpr (BLOCK) {
       if (e >= in.bl1 || crank + C * row >= in.bl2) {  // outside the caller's block: stays 0
         flag = false;
@@ -1040,21 +1068,41 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
       (void)save_t;
     }
     flag = was_live || (g.x * g.x + g.y * g.y > kap * kap);
+    // the sparse variant writes its result from the last epilogue (no dense grid to copy from)
+    if constexpr (SPARSE) {
+      if (last && !flag) c_out[(crank + C * row) * L1 + e] = make_float2(0.f, 0.f);
+    } else {
+      (void)last;
+    }
     return flag ? g : make_float2(0.f, 0.f);
   };
   // ext: a flagged element, in ascending o; returns z^(t+1), the next FFT input
-  auto ext = [&](int row, int e, int o, float2 g, float beta, float kap) -> float2 {
+  auto ext = [&](int row, int e, int o, float2 g, float beta, float kap, bool last) -> float2 {
     const int sidx = row * L1 + e;
     const int gidx = (crank + C * row) * L1 + e;
     float2 c_old = make_float2(0.f, 0.f), x = make_float2(0.f, 0.f);  // c^(t-1), z^(t)
     float2 cl = make_float2(0.f, 0.f), zl = make_float2(0.f, 0.f);
     if ((live >> o) & 1u) {
-      c_old = cta.s0[sidx];
-      x = cta.s1[sidx];
-      if (!first) {
-        const uint2 w = rank_old == 0 ? slot_old0 : rank_old == 1 ? slot_old1 : lo[gidx];
-        cl = unpack_bf16x2(w.x);
-        zl = unpack_bf16x2(w.y);
+      if constexpr (SPARSE) {
+        if (first) {
+          c_old = x = c0 ? c0[gidx] : make_float2(0.f, 0.f);  // c^(0), z^(1) = c^(0); exact
+        } else {
+          const int k = (set * 2 + rank_old) * T + (int)threadIdx.x;
+          const float4 h = rank_old < 2 ? shi[k] : hi[gidx];
+          const uint2 w = rank_old < 2 ? slo[k] : lo[gidx];
+          c_old = make_float2(h.x, h.y);
+          x = make_float2(h.z, h.w);
+          cl = unpack_bf16x2(w.x);
+          zl = unpack_bf16x2(w.y);
+        }
+      } else {
+        c_old = cta.s0[sidx];
+        x = cta.s1[sidx];
+        if (!first) {
+          const uint2 w = rank_old == 0 ? slot_old0 : rank_old == 1 ? slot_old1 : lo[gidx];
+          cl = unpack_bf16x2(w.x);
+          zl = unpack_bf16x2(w.y);
+        }
       }
       ++rank_old;
     }
@@ -1074,14 +1122,31 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
     float zxh, zxl, zyh, zyl;  // z^(t+1) = c^(t) + beta_t (c^(t) - c^(t-1))
     dd_axpy(beta, dxh, dxl, cxh, cxl, zxh, zxl);
     dd_axpy(beta, dyh, dyl, cyh, cyl, zyh, zyl);
-    cta.s0[sidx] = make_float2(cxh, cyh);
-    cta.s1[sidx] = make_float2(zxh, zyh);
+    if constexpr (SPARSE) {
+      if (last) c_out[gidx] = make_float2(cxh, cyh);
+    } else {
+      cta.s0[sidx] = make_float2(cxh, cyh);
+      cta.s1[sidx] = make_float2(zxh, zyh);
+      (void)last;
+    }
     if ((cxh != 0.f) | (cyh != 0.f) | (zxh != 0.f) | (zyh != 0.f)) {
       const uint2 w = make_uint2(pack_bf16x2(cxl, cyl), pack_bf16x2(zxl, zyl));
-      if (rank_new < 2)
-        slot[rank_new] = w;
-      else
-        lo[gidx] = w;
+      if constexpr (SPARSE) {
+        const float4 h = make_float4(cxh, cyh, zxh, zyh);
+        if (rank_new < 2) {
+          const int k = ((set ^ 1) * 2 + rank_new) * T + (int)threadIdx.x;
+          shi[k] = h;
+          slo[k] = w;
+        } else {
+          hi[gidx] = h;
+          lo[gidx] = w;
+        }
+      } else {
+        if (rank_new < 2)
+          slot[rank_new] = w;
+        else
+          lo[gidx] = w;
+      }
       ++rank_new;
       live_next |= 1u << o;
     }
@@ -1115,11 +1180,18 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
 
   if constexpr (S::SQ16) {
     const int nz = kc / 16;
-    cta.sq_fwd1_from_work();
+    // the row stages run over S::PASSES bands of S::BAND rows (one band unless SPARSE)
+    for (int b = 0; b < S::PASSES; ++b) {
+      cta.band = b;
+      cta.sq_fwd1_from_work();
+    }
     for (int it = 0; it < a.iters; ++it) {
       const float beta = a.beta ? __ldg(&a.beta[it]) : 0.0f;
       const bool last = (it == a.iters - 1);
-      cta.sq_fwd2(nz);
+      for (int b = 0; b < S::PASSES; ++b) {
+        cta.band = b;
+        cta.sq_fwd2(nz);
+      }
       __syncthreads();
       cta.template col_dft<false>(kc);
       cluster_barrier<C>();
@@ -1127,17 +1199,26 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
       cluster_barrier<C>();
       cta.template col_dft<true>(kc);
       __syncthreads();
-      if (nz > 2) cta.sq_inv1(nz);
+      if (nz > 2) {
+        for (int b = 0; b < S::PASSES; ++b) {
+          cta.band = b;
+          cta.sq_inv1(nz);
+        }
+      }
       float sc, kap;
       float2* save_t;
       layer(it, sc, kap, save_t);
       if constexpr (ADMM) {
+        cta.band = 0;
         cta.sq_inv2_epi_fwd1([&](int row, int e, float2 g) { return update_admm(row, e, g, last, kap); }, !last, nz);
       } else {
         epilogue_begin();
-        cta.sq_inv2_split_fwd1(
-            [&](int row, int e, int o, float2 g, bool& f) { return quick(row, e, o, g, f, sc, kap, save_t); },
-            [&](int row, int e, int o, float2 g) { return ext(row, e, o, g, beta, kap); }, !last, nz);
+        for (int b = 0; b < S::PASSES; ++b) {
+          cta.band = b;
+          cta.sq_inv2_split_fwd1(
+              [&](int row, int e, int o, float2 g, bool& f) { return quick(row, e, o, g, f, sc, kap, save_t, last); },
+              [&](int row, int e, int o, float2 g) { return ext(row, e, o, g, beta, kap, last); }, !last, nz);
+        }
         epilogue_end();
       }
     }
@@ -1173,7 +1254,7 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
             [&](int row, int e, float2 g) {
               bool f;
               const int o = ord++;
-              cta.work[row * P + pad16(e)] = quick(row, e, o, g, f, sc, kap, save_t);
+              cta.work[row * P + pad16(e)] = quick(row, e, o, g, f, sc, kap, save_t, last);
               if (f) flagged |= 1u << o;
             },
             kc);
@@ -1183,7 +1264,7 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
           int row, e;
           cta.last_row_output(o, row, e);
           float2* w = &cta.work[row * P + pad16(e)];
-          *w = ext(row, e, o, *w, beta, kap);
+          *w = ext(row, e, o, *w, beta, kap, last);
         }
         if constexpr (S::ROW_WARP)
           __syncwarp();
@@ -1194,11 +1275,13 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
     }
   }
 
-  // ---- write the result
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < E; idx += T) {
-    const int s = idx / L1, e = idx % L1;
-    c_out[(crank + C * s) * L1 + e] = cta.s0[idx];
+  // ---- write the result (the sparse variant wrote it in the last epilogue)
+  if constexpr (!SPARSE) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < E; idx += T) {
+      const int s = idx / L1, e = idx % L1;
+      c_out[(crank + C * s) * L1 + e] = cta.s0[idx];
+    }
   }
   // no CTA may leave while a peer can still address its shared memory
   if constexpr (C > 1) cg::this_cluster().sync();
@@ -1208,26 +1291,26 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE>::T, FusedShape<
 // host-side launch table
 // ------------------------------------------------------------------------------------------
 struct FusedEntry {
-  int L1, L2, admm, tile, block;
+  int L1, L2, admm, tile, block, sparse;
   int cluster, threads, smem;
   cudaError_t (*launch)(const FusedArgs&, int n_inst, cudaStream_t);
   cudaError_t (*prepare)();
 };
 
-template <int L1, int L2, bool ADMM, int TILE, bool LEARN = false, bool BLOCK = false>
+template <int L1, int L2, bool ADMM, int TILE, bool LEARN = false, bool BLOCK = false, bool SPARSE = false>
 cudaError_t fused_prepare() {
-  using S = FusedShape<L1, L2, ADMM, TILE>;
-  cudaError_t e = cudaFuncSetAttribute(fused_solve_kernel<L1, L2, ADMM, TILE, LEARN, BLOCK>,
+  using S = FusedShape<L1, L2, ADMM, TILE, SPARSE>;
+  cudaError_t e = cudaFuncSetAttribute(fused_solve_kernel<L1, L2, ADMM, TILE, LEARN, BLOCK, SPARSE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
   if (e == cudaSuccess && S::C > 8)
-    e = cudaFuncSetAttribute(fused_solve_kernel<L1, L2, ADMM, TILE, LEARN, BLOCK>,
+    e = cudaFuncSetAttribute(fused_solve_kernel<L1, L2, ADMM, TILE, LEARN, BLOCK, SPARSE>,
                              cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   return e;
 }
 
-template <int L1, int L2, bool ADMM, int TILE, bool LEARN = false, bool BLOCK = false>
+template <int L1, int L2, bool ADMM, int TILE, bool LEARN = false, bool BLOCK = false, bool SPARSE = false>
 cudaError_t fused_launch(const FusedArgs& a, int n_inst, cudaStream_t st) {
-  using S = FusedShape<L1, L2, ADMM, TILE>;
+  using S = FusedShape<L1, L2, ADMM, TILE, SPARSE>;
   if (n_inst <= 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(n_inst * S::C), 1, 1);
@@ -1241,14 +1324,16 @@ cudaError_t fused_launch(const FusedArgs& a, int n_inst, cudaStream_t st) {
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, fused_solve_kernel<L1, L2, ADMM, TILE, LEARN, BLOCK>, a);
+  return cudaLaunchKernelEx(&cfg, fused_solve_kernel<L1, L2, ADMM, TILE, LEARN, BLOCK, SPARSE>, a);
 }
 
-template <int L1, int L2, bool ADMM, int TILE = kFusedTileElems, bool LEARN = false, bool BLOCK = false>
+template <int L1, int L2, bool ADMM, int TILE = kFusedTileElems, bool LEARN = false, bool BLOCK = false,
+          bool SPARSE = false>
 FusedEntry fused_entry() {
-  using S = FusedShape<L1, L2, ADMM, TILE>;
-  return FusedEntry{L1,       L2, ADMM ? 1 : 0, TILE, BLOCK ? 1 : 0, S::C, S::T, S::SMEM,
-                    &fused_launch<L1, L2, ADMM, TILE, LEARN, BLOCK>, &fused_prepare<L1, L2, ADMM, TILE, LEARN, BLOCK>};
+  using S = FusedShape<L1, L2, ADMM, TILE, SPARSE>;
+  return FusedEntry{L1,      L2,      ADMM ? 1 : 0, TILE, BLOCK ? 1 : 0, SPARSE ? 1 : 0, S::C, S::T, S::SMEM,
+                    &fused_launch<L1, L2, ADMM, TILE, LEARN, BLOCK, SPARSE>,
+                    &fused_prepare<L1, L2, ADMM, TILE, LEARN, BLOCK, SPARSE>};
 }
 
 }  // namespace bccb

@@ -71,6 +71,7 @@ struct bccb_solver {
   float* d_mult = nullptr;      // FP32 Fourier multiplier (includes 1/(L1 L2))
   float2* d_cterm = nullptr;    // FP32 Fourier-domain constant term Bt
   uint2* d_lo = nullptr;        // fused ISTA/FISTA: low-order parts of the state, packed like c
+  float4* d_hi = nullptr;       // sparse-state variant: high parts {c, z} beyond its slots, packed like c
   bccb::InstParams* d_par = nullptr;
   bccb::FusedInst* d_fused = nullptr;
   int* d_ids = nullptr;
@@ -152,7 +153,8 @@ cudaError_t run_multipass(bccb_solver* s, const int* ids, int count, int iters, 
                           void* aux, cudaStream_t stream);
 // fused_inst.cu / fused_dispatch.cu: tile 0 = the default 8192-element tile
 // block: the variant for the circulant embedding of a Toeplitz Gram (ISTA/FISTA, sides >= 32)
-const FusedEntry* fused_lookup(int L1, int L2, bool admm, int tile = 0, bool block = false);
+// sparse: the ISTA/FISTA variant with the state outside shared memory (rows of 256, tile 8192)
+const FusedEntry* fused_lookup(int L1, int L2, bool admm, int tile = 0, bool block = false, bool sparse = false);
 const AdjointEntry* adjoint_lookup(int L1, int L2);
 // the unrolled network's forward kernel (square grids L1 = L2, FISTA, default tile)
 const FusedEntry* learned_lookup(int L1, int L2);

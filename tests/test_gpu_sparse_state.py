@@ -1,0 +1,80 @@
+"""The fused ISTA/FISTA variant whose state lives only at its nonzero positions (per-thread
+slots, global memory beyond them) and whose CTAs run two bands of rows, so that two CTAs of
+8192 grid elements share an SM: the same mathematics and the same arithmetic as the 8192-element
+tile with the state in shared memory, so its results equal that tile's bit for bit, and the
+oracle's within the parity bar.  Forced through the tuner's cache file."""
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import assert_parity, inst, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_name():
+    import torch
+
+    return torch.cuda.get_device_name(0).replace(" ", "_")
+
+
+def _solve(lib, snaps, lams, algo, iters, sparse, tmp_path, c0=None, frac=False):
+    import torch
+
+    cache = tmp_path / f"variant_{sparse}.txt"
+    cache.write_text("".join(f"{_gpu_name()} {s.L1} {s.L2} 0 8192 {sparse}\n" for s in snaps))
+    solver = lib.BatchSolver([inst(s, l, lam_is_frac=frac) for s, l in zip(snaps, lams)], algo)
+    y = torch.from_numpy(solver.y_host).cuda()
+    lib.bccb_batch_tune(solver.handle, y, 3, str(cache))
+    for s in snaps:
+        assert lib.bccb_batch_variant(solver.handle, s.L1, s.L2) == (8192, sparse)
+    c = torch.full((solver.total_c,), 5.0 + 5.0j, dtype=torch.complex64, device="cuda")  # overwritten
+    c0_t = None if c0 is None else torch.from_numpy(np.asarray(c0, np.complex64)).cuda()
+    solver.solve(y, iters, c, c0=c0_t, check=True)
+    torch.cuda.synchronize()
+    out = [g.reshape(-1) for g in solver.unpack(c.cpu().numpy())]
+    res = solver.results()
+    solver.close()
+    return out, res
+
+
+@pytest.mark.parametrize("algo", ["fista", "ista"])
+def test_sparse_state_matches_oracle_and_dense_tile(lib, algo, tmp_path):
+    # rows of 256 with 256, 128, 64 and 32 rows (8, 4, 2 and 1 CTAs per instance)
+    snaps = [synth.config_snapshot(2, 5), synth.make_snapshot(93, 32, 16, 200, 256, 128, 4, 12.0),
+             synth.make_snapshot(94, 24, 8, 90, 256, 64, 3, 15.0), synth.make_snapshot(95, 20, 6, 60, 256, 32, 2, 20.0)]
+    iters = 300
+    refs = [oracle_run(s, algo, iters) for s in snaps]
+    lams = [r["lam"] for r in refs]
+    sp, res_sp = _solve(lib, snaps, lams, algo, iters, 1, tmp_path)
+    de, res_de = _solve(lib, snaps, lams, algo, iters, 0, tmp_path)
+    for i, (a, b, r) in enumerate(zip(sp, de, refs)):
+        assert np.array_equal(a, b), f"{algo} instance {i}: sparse-state and dense-state results differ"
+        assert_parity(a, r, what=f"{algo} sparse state, instance {i}")
+    np.testing.assert_array_equal(res_sp["kkt"], res_de["kkt"])
+
+
+def test_sparse_state_warm_start_and_one_iteration(lib, tmp_path):
+    """A warm start with a dense c0 (every position live in the first iteration, beyond the two
+    slots of each thread), and a single iteration (the result written by the first epilogue)."""
+    s = synth.config_snapshot(2, 6)
+    ref = oracle_run(s, "fista", 40)
+    rng = np.random.default_rng(3)
+    c0 = (rng.standard_normal(65536) + 1j * rng.standard_normal(65536)) * 1e-3
+    c0 = c0.astype(np.complex64)
+    for iters in (1, 40):
+        sp, _ = _solve(lib, [s], [ref["lam"]], "fista", iters, 1, tmp_path, c0=c0)
+        de, _ = _solve(lib, [s], [ref["lam"]], "fista", iters, 0, tmp_path, c0=c0)
+        assert np.array_equal(sp[0], de[0]), f"{iters} iterations from a dense warm start"
+    cold, _ = _solve(lib, [s], [ref["lam"]], "fista", 40, 1, tmp_path)
+    assert_parity(cold[0], ref, what="sparse state, 40 iterations")
+
+
+def test_full_batch_shape_uses_two_ctas_per_sm(lib, tmp_path):
+    """The bench's workload (lam as a fraction) on 152 instances: sparse and dense variants agree
+    bit for bit."""
+    snaps = [synth.make_snapshot(20000 + i, 32, 32, 256, 256, 256, 8, 10.0) for i in range(0, 4096, 27)]
+    sp, _ = _solve(lib, snaps, [0.05] * len(snaps), "fista", 200, 1, tmp_path, frac=True)
+    de, _ = _solve(lib, snaps, [0.05] * len(snaps), "fista", 200, 0, tmp_path, frac=True)
+    for i, (a, b) in enumerate(zip(sp, de)):
+        assert np.array_equal(a, b), f"instance {i}"
