@@ -215,13 +215,18 @@ int bccb_batch_variant(bccb_solver_t s, int L1, int L2, int* tile, int* sparse_s
  * the backward pass; check != 0 runs the FP64 KKT check on c_{K-1}.
  * bccb_unrolled_bwd takes grad_c_dev = dLoss/dc_{K-1} (complex64, packed like c, as
  * dLoss/dRe + j dLoss/dIm) and ADDS dLoss/da_k and dLoss/dt_k, summed over the batch,
- * to the device float64 arrays grad_scale_dev / grad_thresh_dev (length layers).  It
- * needs the same solver, layers, multipliers and saved buffer as the forward call.
+ * to the device float64 arrays grad_scale_dev / grad_thresh_dev (length layers).  If
+ * grad_y_dev is not NULL it also WRITES dLoss/dy there (complex64, packed like y, same
+ * convention): y enters every layer through b = A^H y, and, for instances whose lam is a
+ * fraction of ||A^H y||_inf, every threshold through that maximum (the derivative is taken at
+ * the first cell that attains it).  It needs the same solver, layers, multipliers and saved
+ * buffer as the forward call, with no other solve on the solver in between.
  * Square grids (L1 = L2, up to 256) only; BCCB_ERR_UNSUPPORTED otherwise. */
 int bccb_unrolled_fwd(bccb_solver_t s, const void* y_dev, int batch, int layers, const float* scale_dev,
                       const float* thresh_dev, void* c_out_dev, void* saved_dev, int check);
 int bccb_unrolled_bwd(bccb_solver_t s, int batch, int layers, const float* scale_dev, const float* thresh_dev,
-                      const void* saved_dev, const void* grad_c_dev, double* grad_scale_dev, double* grad_thresh_dev);
+                      const void* saved_dev, const void* grad_c_dev, void* grad_y_dev, double* grad_scale_dev,
+                      double* grad_thresh_dev);
 
 /* Phase timing of bccb_batch_solve, for profiling.  bccb_set_timing(s, 1) makes
  * every later solve record CUDA events on the solver's stream around its three

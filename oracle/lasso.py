@@ -414,11 +414,13 @@ def unrolled_forward(A, y, mu, theta, save=False):
     return (c, zs, us) if save else c
 
 
-def unrolled_backward(A, y, mu, theta, grad_c):
+def unrolled_backward(A, y, mu, theta, grad_c, want_grad_y=False):
     """Reverse-mode derivative of a real loss through ``unrolled_forward``.
 
     Complex gradients use g = dLoss/dRe + j dLoss/dIm, so dLoss = Re(conj(g) dx).
-    Returns (dLoss/dmu_k, dLoss/dtheta_k) as float64 arrays of length K.
+    Returns (dLoss/dmu_k, dLoss/dtheta_k) as float64 arrays of length K; with ``want_grad_y``
+    also dLoss/dy (the thresholds held fixed): every layer sees y through b = A^H y, with
+    du_k/db = mu_k, so g_b = sum_k mu_k g_{u_k} and g_y = A g_b.
     Derivatives used:
       * S_theta at |u| > theta: with s = 1 - theta/|u|,
           g_u = s g_c + (theta/|u|^3) Re(conj(g_c) u) u,   dLoss/dtheta = -Re(conj(g_c) u)/|u|;
@@ -437,6 +439,7 @@ def unrolled_backward(A, y, mu, theta, grad_c):
     d_th = np.zeros(K)
     g_c = np.array(grad_c, dtype=np.complex128)  # gradient w.r.t. c_k (current k)
     g_c_next = np.zeros(L, np.complex128)  # contribution to c_(k-1) from z_(k+1)
+    g_b = np.zeros(L, np.complex128)
     for k in range(K - 1, -1, -1):
         u = us[k]
         mag = np.abs(u)
@@ -448,6 +451,7 @@ def unrolled_backward(A, y, mu, theta, grad_c):
         d_th[k] = -float(np.sum(proj / mag[act]))
         Gz = gram(zs[k])
         d_mu[k] = float(np.real(np.vdot(g_u, b - Gz)))
+        g_b += mu[k] * g_u
         g_z = g_u - mu[k] * gram(g_u)
         # z_k = (1 + beta_(k-1)) c_(k-1) - beta_(k-1) c_(k-2), with z_1 = c_0 = 0 constant.
         if k > 0:
@@ -456,4 +460,6 @@ def unrolled_backward(A, y, mu, theta, grad_c):
             g_c_next = -bk * g_z
         else:
             g_c = np.zeros(L, np.complex128)
+    if want_grad_y:
+        return d_mu, d_th, A @ g_b
     return d_mu, d_th

@@ -67,7 +67,7 @@ def _load():
     lib.bccb_batch_tile.argtypes = [vp, i32, i32, P(i32)]
     lib.bccb_batch_variant.argtypes = [vp, i32, i32, P(i32), P(i32)]
     lib.bccb_unrolled_fwd.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, i32]
-    lib.bccb_unrolled_bwd.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp]
+    lib.bccb_unrolled_bwd.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp]
     lib.bccb_batch_peaks.argtypes = [vp, vp, i32, dbl, vp, vp, vp, vp, vp]
     lib.bccb_batch_set_method.argtypes = [vp, i32]
     lib.bccb_batch_size.argtypes = [vp, P(i32)]
@@ -243,9 +243,10 @@ def bccb_unrolled_fwd(h: int, y_dev, batch: int, layers: int, scale_dev, thresh_
 
 
 def bccb_unrolled_bwd(h: int, batch: int, layers: int, scale_dev, thresh_dev, saved_dev, grad_c_dev,
-                      grad_scale_dev, grad_thresh_dev) -> None:
+                      grad_scale_dev, grad_thresh_dev, grad_y_dev=None) -> None:
     _raise(_lib.bccb_unrolled_bwd(h, int(batch), int(layers), _ptr(scale_dev), _ptr(thresh_dev), _ptr(saved_dev),
-                                  _ptr(grad_c_dev), _ptr(grad_scale_dev), _ptr(grad_thresh_dev)), h)
+                                  _ptr(grad_c_dev), _ptr(grad_y_dev), _ptr(grad_scale_dev), _ptr(grad_thresh_dev)),
+           h)
 
 
 def bccb_batch_set_method(h: int, method) -> None:

@@ -10,6 +10,10 @@
 //   dLoss/da_k += -Re(conj(g_u) G'_k)
 //   g_z = g_u - a_k mu G g_u      (G is Hermitian: the same BCCB product, without Bt)
 //   g_{c_{k-1}} = (1 + beta_{k-1}) g_z + (carried -beta_k g_z of the layer above)
+// For dLoss/dy (optional): every layer sees b = A^H y through u_k, with du_k/db = a_k mu, so
+// grad_b collects sum_k a_k g_u (mu is applied afterwards), and grad_lam collects, per instance,
+// sum_k t_k dLoss/dtheta_k with theta_k = t_k kappa (the threshold's dependence on b when lam is
+// a fraction of ||b||_inf).
 // The Gram product reuses the fused kernel's transform stages; one cluster per
 // instance, the two gradient grids stay in shared memory for all K layers.
 #pragma once
@@ -31,6 +35,8 @@ struct AdjArgs {
   const float2* grad_c;   // dLoss/dc_{K-1}, packed like the solution
   double* grad_scale;     // += dLoss/da_k
   double* grad_thresh;    // += dLoss/dt_k
+  float2* grad_b;         // nullable: sum_k a_k g_{u_k}, packed like the solution (overwritten)
+  double* grad_lam;       // with grad_b: += sum_k t_k dLoss/dtheta_k per instance (zeroed by the caller)
   int layers;
   int pad_;
 };
@@ -71,7 +77,8 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, false, TILE>::T, FusedShape
   if constexpr (C > 1) crank = (int)cg::this_cluster().block_rank();
   cta.crank = crank;
 
-  const FusedInst in = a.insts[a.ids[blockIdx.x / C]];
+  const int inst_id = a.ids[blockIdx.x / C];
+  const FusedInst in = a.insts[inst_id];
   const float kappa = in.kappa;
   const int kc = min(L1, (in.kcols + 15) & ~15);
   const float* mult = a.mult + in.g_off;
@@ -115,9 +122,15 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, false, TILE>::T, FusedShape
       d_a -= gu.x * g.x + gu.y * g.y;
       cta.s0[idx] = gu;
       cta.work[s * P + pad16(e)] = gu;
+      if (a.grad_b) {
+        float2* gb = a.grad_b + in.c_off + gidx;
+        const float2 prev = (k == a.layers - 1) ? make_float2(0.f, 0.f) : *gb;
+        *gb = make_float2(prev.x + ak * gu.x, prev.y + ak * gu.y);
+      }
     }
     warp_add_to(&a.grad_scale[k], d_a);
     warp_add_to(&a.grad_thresh[k], d_t * kappa);
+    if (a.grad_b) warp_add_to(&a.grad_lam[inst_id], d_t * __ldg(&a.thresh[k]));
     __syncthreads();
     // g_z = g_u - a_k mu G g_u, then the momentum chain
     const float bk = (k > 0) ? __ldg(&a.beta[k - 1]) : 0.f;

@@ -99,7 +99,7 @@ void release(bccb_solver* s) {
                   s->d_kkt,    s->d_obj,      s->d_red,     s->d_tw32,    s->d_tw64,    s->d_y_stage,
                   s->d_c_stage, s->d_mult64,  s->d_bt64,    s->d_mp_work, s->d_mp_s0,   s->d_mp_s1,
                   s->d_cint,   s->d_c0int,    s->d_toep_h,  s->d_toep_fb, s->d_lam_sel, s->d_lam_src,
-                  s->d_lo,     s->d_hi};
+                  s->d_lo,     s->d_hi,       s->d_gradb,   s->d_gradlam};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -937,7 +937,8 @@ int bccb_unrolled_fwd(bccb_solver_t s, const void* y_dev, int batch, int layers,
 }
 
 int bccb_unrolled_bwd(bccb_solver_t s, int batch, int layers, const float* scale_dev, const float* thresh_dev,
-                      const void* saved_dev, const void* grad_c_dev, double* grad_scale_dev, double* grad_thresh_dev) {
+                      const void* saved_dev, const void* grad_c_dev, void* grad_y_dev, double* grad_scale_dev,
+                      double* grad_thresh_dev) {
   if (!s) return fail(nullptr, BCCB_ERR_INVALID_ARG, "solver is NULL");
   s->last_error.clear();
   if (batch != s->n) return fail(s, BCCB_ERR_INVALID_ARG, "batch differs from the solver's instance count");
@@ -960,6 +961,13 @@ int bccb_unrolled_bwd(bccb_solver_t s, int batch, int layers, const float* scale
   a.grad_scale = grad_scale_dev;
   a.grad_thresh = grad_thresh_dev;
   a.layers = layers;
+  if (grad_y_dev) {
+    if (!s->d_gradb) BCCB_CUDA(s, dalloc(&s->d_gradb, s->total_c));
+    if (!s->d_gradlam) BCCB_CUDA(s, dalloc(&s->d_gradlam, s->n));
+    BCCB_CUDA(s, cudaMemsetAsync(s->d_gradlam, 0, sizeof(double) * s->n, s->stream));
+    a.grad_b = s->d_gradb;
+    a.grad_lam = s->d_gradlam;
+  }
   for (const auto& c : s->classes) {
     const bccb::AdjointEntry* ae = bccb::adjoint_lookup(c.entry.L1, c.entry.L2);
     if (!ae) return fail(s, BCCB_ERR_UNSUPPORTED, "no adjoint kernel for this grid");
@@ -967,6 +975,7 @@ int bccb_unrolled_bwd(bccb_solver_t s, int batch, int layers, const float* scale
     a.ids = s->d_ids + c.first;
     BCCB_CUDA(s, ae->launch(a, c.count, s->stream));
   }
+  if (grad_y_dev) BCCB_CUDA(s, bccb::unrolled_grad_y(s, s->d_gradb, s->d_gradlam, grad_y_dev));
   return BCCB_OK;
 }
 

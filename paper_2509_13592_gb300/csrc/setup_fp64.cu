@@ -650,6 +650,89 @@ __global__ void toep_crop_kernel(const InstDesc* __restrict__ desc, const C* __r
     cu[d.u_off + t] = ci[d.c_off + (t % d.bL1) + (int64_t)(t / d.bL1) * d.L1];
 }
 
+
+// ---- dLoss/dy of the unrolled network (bccb_unrolled_bwd): b = A^H y enters every layer, so
+// with g_b = dLoss/db, g_y = A g_b, and (A v)_n = (-1)^(m1+m2) FFT2(v)[m2 mod L2][m1 mod L1]
+// (the unnormalised forward DFT; A's columns are exp(-j 2 pi f.m) with f = -1/2 + l/L).
+
+// w = mu * (sum_k a_k g_{u_k}): the layers' part of g_b
+__global__ void gy_load_kernel(const InstDesc* __restrict__ desc, const InstParams* __restrict__ par,
+                               const float2* __restrict__ grad_b, double2* w) {
+  const InstDesc d = desc[blockIdx.x];
+  const double mu = par[blockIdx.x].mu;
+  for (int cell = blockIdx.y * blockDim.x + threadIdx.x; cell < d.L1 * d.L2; cell += gridDim.y * blockDim.x) {
+    const float2 g = grad_b[d.c_off + cell];
+    w[d.g_off + cell] = make_double2(mu * (double)g.x, mu * (double)g.y);
+  }
+}
+
+// lam = frac ||b||_inf: the thresholds t_k mu lam depend on b through its largest entry i*,
+// d lam / d b = frac b_i*/|b_i*| (first index among equal maxima), and dLoss/dlam = mu * gl with
+// gl = sum_k t_k dLoss/dtheta_k; one block per instance
+__global__ void gy_lam_kernel(const InstDesc* __restrict__ desc, const InstParams* __restrict__ par,
+                              const double2* __restrict__ b64, const double* __restrict__ grad_lam, double2* w) {
+  __shared__ double sv[32];
+  __shared__ int si[32];
+  const InstDesc d = desc[blockIdx.x];
+  if (!d.lam_is_frac) return;
+  const int L = d.L1 * d.L2;
+  double best = -1.0;
+  int bi = 0;
+  for (int cell = threadIdx.x; cell < L; cell += blockDim.x) {
+    const double2 v = b64[d.g_off + cell];
+    const double m = v.x * v.x + v.y * v.y;
+    if (m > best) {  // cells ascend per thread: the first maximum wins
+      best = m;
+      bi = cell;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) {
+      best = ob;
+      bi = oi;
+    }
+  }
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    sv[wid] = best;
+    si[wid] = bi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k)
+      if (sv[k] > best || (sv[k] == best && si[k] < bi)) {
+        best = sv[k];
+        bi = si[k];
+      }
+    if (best > 0.0) {
+      const double2 v = b64[d.g_off + bi];
+      const double r = sqrt(best);
+      const double f = d.lam * par[blockIdx.x].mu * grad_lam[blockIdx.x] / r;
+      double2 t = w[d.g_off + bi];
+      t.x += f * v.x;
+      t.y += f * v.y;
+      w[d.g_off + bi] = t;
+    }
+  }
+}
+
+// g_y[n] = (-1)^(m1 + m2) W[m2 mod L2][m1 mod L1] for every kept element n at (m1, m2)
+__global__ void gy_gather_kernel(const InstDesc* __restrict__ desc, const int* __restrict__ mask_idx,
+                                 const double2* __restrict__ w, float2* grad_y) {
+  const InstDesc d = desc[blockIdx.x];
+  const int* mi = mask_idx + d.mask_off;
+  for (int p = blockIdx.y * blockDim.x + threadIdx.x; p < d.M1 * d.M2; p += gridDim.y * blockDim.x) {
+    const int n = mi[p];
+    if (n < 0) continue;
+    const int m1 = p % d.M1, m2 = p / d.M1;
+    const double2 v = w[d.g_off + (m2 % d.L2) * d.L1 + (m1 % d.L1)];
+    const double sg = ((m1 + m2) & 1) ? -1.0 : 1.0;
+    grad_y[d.y_off + n] = make_float2((float)(sg * v.x), (float)(sg * v.y));
+  }
+}
+
 }  // namespace
 
 cudaError_t fill_twiddles(bccb_solver* s) {
@@ -744,6 +827,18 @@ cudaError_t run_check(bccb_solver* s, const void* y_dev, const void* c_dev) {
   if (s->prec == 1)
     return run_check_t<double2>(s, static_cast<const double2*>(y_dev), static_cast<const double2*>(c_dev));
   return run_check_t<float2>(s, static_cast<const float2*>(y_dev), static_cast<const float2*>(c_dev));
+}
+
+cudaError_t unrolled_grad_y(bccb_solver* s, const float2* grad_b, const double* grad_lam, void* grad_y) {
+  const dim3 gc = grid_cells(s);
+  gy_load_kernel<<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_par, grad_b, s->d_w64);
+  gy_lam_kernel<<<s->n, kThreads, 0, s->stream>>>(s->d_desc, s->d_par, s->d_b64, grad_lam, s->d_w64);
+  cudaError_t err;
+  if ((err = fft2_64(s, s->d_w64, 0)) != cudaSuccess) return err;
+  gy_gather_kernel<<<gc, kThreads, 0, s->stream>>>(s->d_desc, s->d_mask_idx, s->d_w64,
+                                                    static_cast<float2*>(grad_y));
+  s->launches += 3;
+  return cudaGetLastError();
 }
 
 cudaError_t prepare_fp64_passes(int max_L2) {

@@ -72,6 +72,8 @@ struct bccb_solver {
   float2* d_cterm = nullptr;    // FP32 Fourier-domain constant term Bt
   uint2* d_lo = nullptr;        // fused ISTA/FISTA: low-order parts of the state, packed like c
   float4* d_hi = nullptr;       // sparse-state variant: high parts {c, z} beyond its slots, packed like c
+  float2* d_gradb = nullptr;    // unrolled backward with dLoss/dy: sum_k a_k g_{u_k}, packed like c
+  double* d_gradlam = nullptr;  // and per instance sum_k t_k dLoss/dtheta_k
   bccb::InstParams* d_par = nullptr;
   bccb::FusedInst* d_fused = nullptr;
   int* d_ids = nullptr;
@@ -145,6 +147,9 @@ cudaError_t run_setup(bccb_solver* s, const void* y_dev);
 cudaError_t run_check(bccb_solver* s, const void* y_dev, const void* c_dev);
 cudaError_t fill_twiddles(bccb_solver* s);
 cudaError_t fista_schedule(bccb_solver* s, int iters);
+// dLoss/dy of the unrolled network from the adjoint's b-gradient (sum_k a_k g_{u_k}, packed like c)
+// and per-instance sum_k t_k dLoss/dtheta_k; uses the last setup's mu, b and Lambda workspace
+cudaError_t unrolled_grad_y(bccb_solver* s, const float2* grad_b, const double* grad_lam, void* grad_y);
 // shared-memory opt-in of the FP64 column pass for grids with up to max_L2 rows
 cudaError_t prepare_fp64_passes(int max_L2);
 // multipass.cu: all iterations of one multi-pass class (ids[0..count)) on `stream`

@@ -49,13 +49,15 @@ class UnrolledNet:
 
 class UnrolledFISTA(torch.autograd.Function):
     """c_{K-1} = Net(y; a, t).  y: packed complex64 (batch * N) on the GPU; scale = a, thresh = t:
-    float32 (K,) on the GPU.  Returns the packed complex64 (batch * L1 * L2) output."""
+    float32 (K,) on the GPU.  Returns the packed complex64 (batch * L1 * L2) output.  The backward
+    gives dLoss/da, dLoss/dt and, when y requires a gradient, dLoss/dy (PyTorch's convention for
+    complex tensors, dLoss/dRe + j dLoss/dIm, is the library's)."""
 
     @staticmethod
     def forward(ctx, y, scale, thresh, net):
         K = scale.numel()
         c = torch.empty(net.batch * net.L, dtype=torch.complex64, device=y.device)
-        need = ctx.needs_input_grad[1] or ctx.needs_input_grad[2]
+        need = ctx.needs_input_grad[0] or ctx.needs_input_grad[1] or ctx.needs_input_grad[2]
         saved = torch.empty(K * 2 * net.batch * net.L, dtype=torch.complex64, device=y.device) if need else None
         B.bccb_unrolled_fwd(net.handle, y, net.batch, K, scale.detach().contiguous(), thresh.detach().contiguous(),
                             c, saved)
@@ -70,9 +72,11 @@ class UnrolledFISTA(torch.autograd.Function):
         K = scale.numel()
         g_s = torch.zeros(K, dtype=torch.float64, device=scale.device)
         g_t = torch.zeros(K, dtype=torch.float64, device=scale.device)
+        g_y = torch.empty(ctx.net.batch * ctx.net.N, dtype=torch.complex64, device=scale.device) \
+            if ctx.needs_input_grad[0] else None
         B.bccb_unrolled_bwd(ctx.net.handle, ctx.net.batch, K, scale.contiguous(), thresh.contiguous(), ctx.saved,
-                            grad_c.contiguous().to(torch.complex64), g_s, g_t)
-        return None, g_s.to(scale.dtype), g_t.to(thresh.dtype), None
+                            grad_c.contiguous().to(torch.complex64), g_s, g_t, g_y)
+        return g_y, g_s.to(scale.dtype), g_t.to(thresh.dtype), None
 
 
 def net_forward(net: UnrolledNet, y, scale, thresh):
@@ -153,15 +157,20 @@ def snapshot_batch(cfg: TrainConfig, mask, first, count):
     return torch.from_numpy(np.concatenate(ys)).cuda()
 
 
-def plain_fista(cfg: TrainConfig, mask, y, iters, batch):
-    inst = dict(M1=cfg.M1, M2=cfg.M2, L1=cfg.L1, L2=cfg.L2, mask=mask, y=np.zeros(cfg.N, np.complex64),
-                lam=cfg.lam_frac, lam_is_frac=True)
-    s = B.BatchSolver([inst] * batch, "fista")
+def plain_fista(cfg: TrainConfig, mask, y, iters, batch, solver=None):
+    """Plain batched FISTA on `batch` snapshots of the fixed array (a solver of that batch may be
+    passed in and is then reused)."""
+    s = solver
+    if s is None:
+        inst = dict(M1=cfg.M1, M2=cfg.M2, L1=cfg.L1, L2=cfg.L2, mask=mask, y=np.zeros(cfg.N, np.complex64),
+                    lam=cfg.lam_frac, lam_is_frac=True)
+        s = B.BatchSolver([inst] * batch, "fista")
     out = torch.empty(batch * cfg.L1 * cfg.L2, dtype=torch.complex64, device="cuda")
     torch.cuda.synchronize()
     s.solve(y, iters, out, check=False)
     torch.cuda.synchronize()
-    s.close()
+    if solver is None:
+        s.close()
     return out
 
 
@@ -183,11 +192,14 @@ def train(cfg: TrainConfig, resume: bool = False, log=print):
         opt.load_state_dict(ck["opt"])
         step0 = int(ck["step"])
     history = []
+    inst = dict(M1=cfg.M1, M2=cfg.M2, L1=cfg.L1, L2=cfg.L2, mask=mask, y=np.zeros(cfg.N, np.complex64),
+                lam=cfg.lam_frac, lam_is_frac=True)
+    target_solver = B.BatchSolver([inst] * cfg.batch, "fista")
     for step in range(step0, cfg.steps):
         first = cfg.first_snapshot + step * cfg.batch
         y = snapshot_batch(cfg, mask, first, cfg.batch)
         with torch.no_grad():
-            target = plain_fista(cfg, mask, y, cfg.target_iters, cfg.batch)
+            target = plain_fista(cfg, mask, y, cfg.target_iters, cfg.batch, target_solver)
         c = net_forward(net, y, log_a.exp(), log_t.exp())
         loss = (relative_errors(c, target, cfg.batch, net.L) ** 2).mean()
         opt.zero_grad()
@@ -200,6 +212,7 @@ def train(cfg: TrainConfig, resume: bool = False, log=print):
             torch.save({"log_a": log_a.detach(), "log_t": log_t.detach(), "opt": opt.state_dict(), "step": step + 1},
                        cfg.checkpoint)
     net.close()
+    target_solver.close()
     return log_a.detach().exp(), log_t.detach().exp(), history
 
 
@@ -266,6 +279,7 @@ if __name__ == "__main__":
     ap.add_argument("--eval", type=int, default=8192)
     ap.add_argument("--checkpoint", default=None)
     ap.add_argument("--resume", action="store_true")
+    ap.add_argument("--save", default=None, help="write the trained multipliers and the loss curve (JSON)")
     args = ap.parse_args()
     cfg = TrainConfig(layers=args.layers, batch=args.batch, steps=args.steps, lr=args.lr,
                       checkpoint=args.checkpoint)
@@ -278,4 +292,11 @@ if __name__ == "__main__":
     res.update({"train_steps": args.steps, "train_batch": args.batch, "train_snapshots": args.steps * args.batch,
                 "train_seconds": train_s, "loss_first": hist[0] if hist else None,
                 "loss_last": hist[-1] if hist else None, "scale": a.tolist(), "thresh": t.tolist()})
+    if args.save:
+        with open(args.save, "w") as f:
+            json.dump({"layers": args.layers, "scale": a.tolist(), "thresh": t.tolist(),
+                       "train_snapshots": args.steps * args.batch, "train_batch": args.batch, "lr": args.lr,
+                       "train_seconds": train_s,
+                       "loss_curve": [[i, float(v)] for i, v in enumerate(hist) if i % 10 == 0 or i == len(hist) - 1],
+                       "eval": {k: v for k, v in res.items() if k not in ("scale", "thresh")}}, f, indent=1)
     print(json.dumps(res), flush=True)

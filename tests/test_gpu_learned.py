@@ -151,3 +151,51 @@ def test_training_gain_and_kkt_fallback(lib, tmp_path):
                                            ref.reshape(nb, -1)[idx].reshape(-1), len(idx), net.L)
         assert e_after.mean() < e_before.mean()
     net.close()
+
+
+def test_unrolled_grad_y_matches_finite_differences(lib):
+    """dLoss/dy through the network (bccb_unrolled_bwd's grad_y) against central differences of
+    the FP64 oracle's forward pass in which, as on the GPU, lam = 0.1 ||A^H y||_inf and with it
+    every threshold follows the perturbed measurements."""
+    import torch
+
+    from paper_2509_13592_gb300 import learned
+
+    mask, snaps = _problem(6, count=2)
+    K = 6
+    rng = np.random.default_rng(2)
+    a = (0.8 + 0.4 * rng.random(K)).astype(np.float32)
+    t = (0.6 + 0.8 * rng.random(K)).astype(np.float32)
+    targets = []
+    for s in snaps:
+        A, _, _, _, lam = _oracle_params(s, np.ones(1), np.ones(1))
+        targets.append(oracle.fista(A, s.y, lam, 200))
+    net, y = _net(lib, mask, snaps)
+    y_t = y.clone().requires_grad_(True)
+    c = learned.net_forward(net, y_t, torch.from_numpy(a).cuda(), torch.from_numpy(t).cuda())
+    tgt = torch.from_numpy(np.concatenate(targets).astype(np.complex64)).cuda()
+    ((c - tgt).abs() ** 2).sum().backward()
+    torch.cuda.synchronize()
+    got = y_t.grad.cpu().numpy().reshape(len(snaps), -1)
+    for i, s in enumerate(snaps):
+        A = oracle.dictionary(s.mask, s.M1, s.M2, s.L1, s.L2)
+        mu = oracle.step_size(A)
+        y0 = s.y.astype(np.complex64).astype(np.complex128)  # the measurements the GPU was given
+
+        def loss(yy):
+            lam = 0.1 * oracle.lambda_max(A, yy)
+            ci = oracle.unrolled_forward(A, yy, mu * a.astype(float), mu * lam * t.astype(float))
+            return float(np.sum(np.abs(ci - targets[i]) ** 2))
+
+        h = 1e-6 * np.abs(y0).max()
+        fd = np.zeros(y0.size, np.complex128)
+        for n in range(y0.size):
+            for unit in (1.0, 1j):
+                e = np.zeros(y0.size, np.complex128)
+                e[n] = h * unit
+                d = (loss(y0 + e) - loss(y0 - e)) / (2 * h)
+                fd[n] += d * (1.0 if unit == 1.0 else 1j)
+        scale = np.abs(fd).max()
+        assert scale > 0
+        assert np.abs(got[i] - fd).max() <= 2e-3 * scale, (i, np.abs(got[i] - fd).max() / scale)
+    net.close()

@@ -379,6 +379,34 @@ def test_unrolled_backward_matches_finite_differences():
         assert abs(fd - d_th[k]) <= 1e-5 * max(1.0, abs(fd)), (k, fd, d_th[k])
 
 
+def test_unrolled_grad_y_matches_finite_differences():
+    """dLoss/dy of the unrolled network (thresholds fixed) against central differences on the
+    real and imaginary part of every measurement."""
+    s, A = _small_problem(seed=13, M1=4, M2=4, N=9, L1=8, L2=8, K=2, snr=15.0, on_grid=False)
+    K = 4
+    lam = 0.1 * oracle.lambda_max(A, s.y)
+    mu0 = oracle.step_size(A)
+    rng = np.random.default_rng(1)
+    mu = mu0 * (0.7 + 0.5 * rng.random(K))
+    th = mu0 * lam * (0.5 + rng.random(K))
+    target = oracle.fista(A, s.y, lam, 200)
+
+    def loss(y):
+        c = oracle.unrolled_forward(A, y, mu, th)
+        return float(np.sum(np.abs(c - target) ** 2))
+
+    c = oracle.unrolled_forward(A, s.y, mu, th)
+    _, _, g_y = oracle.unrolled_backward(A, s.y, mu, th, 2.0 * (c - target), want_grad_y=True)
+    h = 1e-7 * np.abs(s.y).max()
+    for n in range(s.y.size):
+        for unit in (1.0, 1j):
+            e = np.zeros(s.y.size, np.complex128)
+            e[n] = h * unit
+            fd = (loss(s.y + e) - loss(s.y - e)) / (2 * h)
+            got = g_y[n].real if unit == 1.0 else g_y[n].imag
+            assert abs(fd - got) <= 1e-5 * max(1.0, abs(fd)), (n, unit, fd, got)
+
+
 def test_column_and_kronecker_helpers_match_dense_dictionary():
     """The large-grid helpers (selected columns, b from the Kronecker factors) equal the dense
     construction on grids where both fit."""
