@@ -223,9 +223,11 @@ def run_reference(args, rank, world):
 
 
 # DRAM traffic of the fused kernel per instance, from one ncu capture of a small case of the
-# variant named here (profiles/fused_solve_256x256_fista_ncu_full.md); None until captured
-FUSED_TRAFFIC_VARIANT = None  # (tile, sparse_state)
-FUSED_DRAM_BYTES_PER_INSTANCE = None
+# variant named here (profiles/fused_solve_256x256_fista_ncu_full.md: 152 instances x 200
+# iterations, dram__bytes_read.sum 177.25 MB + dram__bytes_write.sum 220.29 MB); the bytes do not
+# grow with the iteration count past the dense first iterations, so they scale by instances
+FUSED_TRAFFIC_VARIANT = (8192, 1)  # (tile, sparse_state)
+FUSED_DRAM_BYTES_PER_INSTANCE = (177.252352e6 + 220.285696e6) / 152
 
 
 def load_peaks():
