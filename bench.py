@@ -329,7 +329,7 @@ def run_gpu(args, rank, world, local_rank):
         sub = insts[:n_s]
         gpu_name = torch.cuda.get_device_name(local_rank).replace(" ", "_")
         with tempfile.NamedTemporaryFile("w", suffix=".txt", delete=False) as f:
-            f.write(f"{gpu_name} 256 256 0 {tile}\n")
+            f.write(f"{gpu_name} 256 256 0 {tile} {sparse_state}\n")
             cache = f.name
         batched = c_dev.view(-1)[: n_s * 65536].reshape(n_s, 65536).clone()
         refs, single_ms = [], []

@@ -339,6 +339,17 @@ struct FusedCta {
   // ---------------------------------------------------------------------------------------
   template <bool INV>
   __device__ __forceinline__ void col_dft(int kc) {
+    // The split form only where one thread per active column would leave more than three
+    // quarters of the CTA idle (the 256 x 256 grid with 32 active columns: 2 of 16 warps); where
+    // that form keeps the threads busy (rows of 64 or 128 over 256 rows) the shuffles only cost
+    // (13 % slower there), and the sparse-state tile, whose two CTAs per SM belong to different
+    // instances, was 3 % slower with it (A/B on one box).
+    if constexpr (RP == 16 && !S::SPARSE && 4 * QV * 16 < T) {  // kc >= 16 once active
+      if (4 * QV * kc < T) {
+        col_dft_lanes<INV>(kc);
+        return;
+      }
+    }
     if constexpr (RP > 1) {
       constexpr int NB = QV * L1;
       constexpr int NBT = (NB + T - 1) / T;
@@ -354,6 +365,39 @@ struct FusedCta {
 #pragma unroll
           for (int i = 0; i < RP; ++i) work[(g + QV * i) * P + pad16(col)] = v[i];
         }
+      }
+    }
+  }
+
+  // The same local column DFTs for RP = 16, each split over 4 lanes (4 x 4 with a shuffle
+  // transpose, as in the middle stage): lane e of the pair (group g, column col) reads inputs
+  // n = e + 4 i, runs the inner 4-point DFT over i, twiddles by W_16^{e k'}, exchanges across
+  // the pair's lanes, runs the outer 4-point DFT and holds outputs e + 4 k'' -- the rows it
+  // read, so the stage still needs no barrier of its own.  Four times the threads of the
+  // one-thread-per-column form for the few active columns.
+  template <bool INV>
+  __device__ __forceinline__ void col_dft_lanes(int kc) {
+    const int np = QV * kc;  // active (group, column) pairs
+    const int lane = tid & 31, e = tid & 3;
+    const int rounds = (4 * np + T - 1) / T;
+    for (int rd = 0; rd < rounds; ++rd) {
+      if (rd * T + (tid & ~31) >= 4 * np) break;  // the whole warp is past the active pairs
+      const int t = rd * T + tid;
+      const bool on = t < 4 * np;
+      const int a = on ? (t >> 2) : 0;
+      const int g = a / kc, col = a % kc;
+      float2* const base = work + g * P + pad16(col);
+      float2 v[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) v[i] = base[(e + 4 * i) * QV * P];
+      dft4<INV>(v[0], v[1], v[2], v[3]);
+#pragma unroll
+      for (int i = 1; i < 4; ++i) v[i] = twmul<INV>(v[i], tw16[e * i]);
+      transpose4(v, e, lane);
+      dft4<INV>(v[0], v[1], v[2], v[3]);  // v[k''] = X[e + 4 k'']
+      if (on) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) base[(e + 4 * k) * QV * P] = v[k];
       }
     }
   }

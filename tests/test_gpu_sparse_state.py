@@ -1,15 +1,19 @@
 """The fused ISTA/FISTA variant whose state lives only at its nonzero positions (per-thread
 slots, global memory beyond them) and whose CTAs run two bands of rows, so that two CTAs of
-8192 grid elements share an SM: the same mathematics and the same arithmetic as the 8192-element
-tile with the state in shared memory, so its results equal that tile's bit for bit, and the
-oracle's within the parity bar.  Forced through the tuner's cache file."""
+8192 grid elements share an SM.  The mathematics of the 8192-element tile with the state in shared
+memory; the local column DFT is summed in another order there (one thread per column here, four
+lanes there), so the two agree to FP32 rounding (2e-5 relative, the compensated state keeps the
+iteration from amplifying it) and each matches the oracle within the parity bar.  Forced through
+the tuner's cache file."""
 import numpy as np
 import pytest
 
 import synth
-from gpu_util import assert_parity, inst, oracle_run
+from gpu_util import assert_parity, inst, oracle_run, rel_err
 
 pytestmark = pytest.mark.gpu
+
+CLOSE = 2e-5  # sparse against dense state: FP32 summation order only
 
 
 def _gpu_name():
@@ -49,9 +53,10 @@ def test_sparse_state_matches_oracle_and_dense_tile(lib, algo, tmp_path):
     sp, res_sp = _solve(lib, snaps, lams, algo, iters, 1, tmp_path)
     de, res_de = _solve(lib, snaps, lams, algo, iters, 0, tmp_path)
     for i, (a, b, r) in enumerate(zip(sp, de, refs)):
-        assert np.array_equal(a, b), f"{algo} instance {i}: sparse-state and dense-state results differ"
+        assert rel_err(a, b) <= CLOSE, f"{algo} instance {i}: sparse and dense state differ by {rel_err(a, b):.2e}"
         assert_parity(a, r, what=f"{algo} sparse state, instance {i}")
-    np.testing.assert_array_equal(res_sp["kkt"], res_de["kkt"])
+        assert_parity(b, r, what=f"{algo} dense state, instance {i}")
+    np.testing.assert_allclose(res_sp["kkt"], res_de["kkt"], rtol=1e-3, atol=1e-6)
 
 
 def test_sparse_state_warm_start_and_one_iteration(lib, tmp_path):
@@ -65,16 +70,16 @@ def test_sparse_state_warm_start_and_one_iteration(lib, tmp_path):
     for iters in (1, 40):
         sp, _ = _solve(lib, [s], [ref["lam"]], "fista", iters, 1, tmp_path, c0=c0)
         de, _ = _solve(lib, [s], [ref["lam"]], "fista", iters, 0, tmp_path, c0=c0)
-        assert np.array_equal(sp[0], de[0]), f"{iters} iterations from a dense warm start"
+        assert rel_err(sp[0], de[0]) <= CLOSE, f"{iters} iterations from a dense warm start"
     cold, _ = _solve(lib, [s], [ref["lam"]], "fista", 40, 1, tmp_path)
     assert_parity(cold[0], ref, what="sparse state, 40 iterations")
 
 
 def test_full_batch_shape_uses_two_ctas_per_sm(lib, tmp_path):
     """The bench's workload (lam as a fraction) on 152 instances: sparse and dense variants agree
-    bit for bit."""
+    to FP32 rounding."""
     snaps = [synth.make_snapshot(20000 + i, 32, 32, 256, 256, 256, 8, 10.0) for i in range(0, 4096, 27)]
     sp, _ = _solve(lib, snaps, [0.05] * len(snaps), "fista", 200, 1, tmp_path, frac=True)
     de, _ = _solve(lib, snaps, [0.05] * len(snaps), "fista", 200, 0, tmp_path, frac=True)
     for i, (a, b) in enumerate(zip(sp, de)):
-        assert np.array_equal(a, b), f"instance {i}"
+        assert rel_err(a, b) <= CLOSE, f"instance {i}: {rel_err(a, b):.2e}"
