@@ -29,6 +29,7 @@ from .lasso import (  # noqa: F401
     admm,
     admm_c_update,
     admm_kron,
+    fista_kron,
     KronDictionary,
     kkt_residual,
     objective,

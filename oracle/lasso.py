@@ -120,6 +120,26 @@ class KronDictionary:
         return S1[np.ix_(self.m1, self.m1)] * S2[np.ix_(self.m2, self.m2)]
 
 
+def fista_kron(K: KronDictionary, y, lam, iters, pre=False):
+    """FISTA (eq:fista) exactly as ``fista`` from c^(0) = 0, with the products with D_s taken through
+    its Kronecker factors and mu = 1/lambda_max(A A^H) from the N x N matrix A A^H.  Returns c^(T)
+    (with ``pre`` also the last soft-threshold argument and the threshold mu*lam)."""
+    mu = 1.0 / float(np.linalg.eigvalsh(K.gram_rows())[-1])
+    b = K.adjoint(y)
+    L = K.shape[1]
+    c_prev = np.zeros(L, np.complex128)
+    z = c_prev.copy()
+    beta = fista_momentum(iters)
+    c = c_prev
+    u = z
+    for t in range(iters):
+        u = z - mu * K.adjoint(K.forward(z)) + mu * b
+        c = soft_threshold(u, mu * lam)
+        z = c + beta[t] * (c - c_prev)
+        c_prev = c
+    return (c, u, mu * lam) if pre else c
+
+
 def admm_kron(K: KronDictionary, y, lam, rho, iters):
     """ADMM (eq:admm) exactly as ``admm``, with every product with D_s taken through its
     Kronecker factors (``KronDictionary``) and the Woodbury form of (A^H A + rho I)^{-1} on

@@ -318,17 +318,17 @@ int create_impl(bccb_solver_t* out, const bccb_inst_t* insts, int n, const uint8
     CREATE_CUDA(bccb::prepare_multipass(s));
   }
   CREATE_CUDA(bccb::fill_twiddles(s));
-  bool any_fused = false, any_sparse = false;
+  bool any_sparse = false;
   for (auto& c : s->classes)
     if (!c.multipass) {
       CREATE_CUDA(c.entry.prepare());
-      any_fused = true;
       any_sparse = any_sparse || (algo != BCCB_ADMM && !blk && bccb::fused_lookup(c.L1, c.L2, false, 0, false, true));
     }
   // the fused ISTA/FISTA kernel keeps the low-order parts of its state here (8 bytes per cell;
   // only cells where the state is nonzero are ever read or written, so no initialisation), and
   // its sparse-state variant the high parts of the positions its slots cannot hold (16 bytes)
-  if (any_fused && algo != BCCB_ADMM) CREATE_CUDA(dalloc(&s->d_lo, s->total_c));
+  // (the FP32 multi-pass solver keeps its low parts here as well)
+  if (prec == BCCB_F32 && algo != BCCB_ADMM) CREATE_CUDA(dalloc(&s->d_lo, s->total_c));
   if (any_sparse) CREATE_CUDA(dalloc(&s->d_hi, s->total_c));
   if (s->classes.size() > 1) {
     CREATE_CUDA(cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming));

@@ -32,6 +32,7 @@ struct MpArgs {
   const V* c0;
   V* c_out;
   V* aux;
+  uint2* lo;  // FP32 ISTA/FISTA: low-order parts {c_lo, z_lo} (bf16 pairs), packed like c_out
   int algo;  // 0 ISTA, 1 FISTA, 2 ADMM
   int it;
   int last;
@@ -110,6 +111,48 @@ __global__ void mp_rows_kernel(MpArgs<V> a) {
         s0[e] = cmk<V>((T)0, (T)0);
         s1[e] = cmk<V>((T)0, (T)0);
         next = cmk<V>((T)0, (T)0);
+      } else if (a.algo != 2 && a.lo) {
+        if constexpr (sizeof(T) == 4) {
+          // FP32: the state in compensated form, as in the fused kernel (c = s0 + c_lo, z = s1 +
+          // z_lo; double-float u, soft-threshold and momentum; ISTA is FISTA with beta = 0, so s1
+          // holds z = c).  The low parts are read only where the state is nonzero and are zero in
+          // the first iteration (an exact warm start).
+          const V c_old = s0[e];
+          const V xin = s1[e];
+          const bool live = (c_old.x != 0.f) | (c_old.y != 0.f) | (xin.x != 0.f) | (xin.y != 0.f);
+          uint2* const lp = a.lo + d.c_off + (int64_t)row * L1 + e;
+          if (!live && !(g.x * g.x + g.y * g.y > kappa * kappa)) {
+            next = cmk<V>((T)0, (T)0);
+          } else {
+            float2 cl = make_float2(0.f, 0.f), zl = make_float2(0.f, 0.f);
+            if (live && a.it > 0) {
+              const uint2 w = *lp;
+              cl = unpack_bf16x2(w.x);
+              zl = unpack_bf16x2(w.y);
+            }
+            float uxh, uxl, uyh, uyl;
+            dd_add(xin.x, zl.x, -g.x, 0.f, uxh, uxl);
+            dd_add(xin.y, zl.y, -g.y, 0.f, uyh, uyl);
+            float cxh = 0.f, cxl = 0.f, cyh = 0.f, cyl = 0.f;
+            const float r2 = uxh * uxh + uyh * uyh;
+            if (r2 > kappa * kappa) {
+              const float kr = kappa * rsqrtf(r2);
+              dd_add(uxh, uxl, -(kr * uxh), 0.f, cxh, cxl);
+              dd_add(uyh, uyl, -(kr * uyh), 0.f, cyh, cyl);
+            }
+            float dxh, dxl, dyh, dyl;
+            dd_add(cxh, cxl, -c_old.x, -cl.x, dxh, dxl);
+            dd_add(cyh, cyl, -c_old.y, -cl.y, dyh, dyl);
+            float zxh, zxl, zyh, zyl;
+            dd_axpy(beta, dxh, dxl, cxh, cxl, zxh, zxl);
+            dd_axpy(beta, dyh, dyl, cyh, cyl, zyh, zyl);
+            s0[e] = cmk<V>(cxh, cyh);
+            s1[e] = cmk<V>(zxh, zyh);
+            if ((cxh != 0.f) | (cyh != 0.f) | (zxh != 0.f) | (zyh != 0.f))
+              *lp = make_uint2(pack_bf16x2(cxl, cyl), pack_bf16x2(zxl, zyl));
+            next = cmk<V>(zxh, zyh);
+          }
+        }
       } else if (a.algo != 2) {
         const V c_old = s0[e];
         const V xin = (a.algo == 1) ? s1[e] : c_old;
@@ -228,6 +271,7 @@ cudaError_t run_t(bccb_solver* s, const int* ids, int count, int iters, const vo
   a.aux = static_cast<V*>(aux);
   a.algo = s->algo;
   a.rho = s->rho;
+  if constexpr (sizeof(T) == 4) a.lo = (s->algo != 2) ? s->d_lo : nullptr;
   const int cells = s->max_L1 * s->max_L2;
   const dim3 gcell((unsigned)count, (unsigned)min(64, (cells + kMpThreads - 1) / kMpThreads));
   const dim3 grow((unsigned)count, (unsigned)s->max_L2);

@@ -34,3 +34,12 @@ def test_admm_equals_the_dense_oracle(rho):
     for a, b in ((z1, z2), (c1, c2), (v1, v2), (u1, u2)):
         np.testing.assert_allclose(b, a, rtol=0, atol=1e-11 * max(1.0, np.abs(a).max()))
     assert k1 == pytest.approx(lam / rho)
+
+
+def test_fista_equals_the_dense_oracle():
+    s = synth.make_snapshot(29, 7, 12, 40, 16, 8, 3, 10.0)  # M2 > L2: the columns fold
+    A = oracle.dictionary(s.mask, 7, 12, 16, 8)
+    K = oracle.KronDictionary(s.mask, 7, 12, 16, 8)
+    lam = 0.1 * oracle.lambda_max(A, s.y)
+    ref = oracle.fista(A, s.y, lam, 250)
+    np.testing.assert_allclose(oracle.fista_kron(K, s.y, lam, 250), ref, rtol=0, atol=1e-11 * np.abs(ref).max())
