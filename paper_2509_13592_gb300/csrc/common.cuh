@@ -27,6 +27,30 @@ __device__ __forceinline__ V cmk(typename ScalarOf<V>::T x, typename ScalarOf<V>
 }
 template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return cmk<V>(a.x + b.x, a.y + b.y); }
 template <typename V> __device__ __forceinline__ V csub(V a, V b) { return cmk<V>(a.x - b.x, a.y - b.y); }
+// complex64 sums as one paired FP32 instruction (add/sub.f32x2, sm_100 and later): half the
+// issue slots of two scalar adds, each lane rounded as a scalar add.  A product that feeds such
+// a sum is no longer fused into it; where that is the common form, twmadd below keeps the fused
+// multiply-adds explicit.
+__device__ __forceinline__ unsigned long long pk2(float2 a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1,%2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+  return r;
+}
+__device__ __forceinline__ float2 upk2(unsigned long long r) {
+  float2 a;
+  asm("mov.b64 {%0,%1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+  return a;
+}
+template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+  return upk2(d);
+}
+template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+  return upk2(d);
+}
 template <typename V> __device__ __forceinline__ V cneg(V a) { return cmk<V>(-a.x, -a.y); }
 template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
   return cmk<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -45,6 +69,13 @@ template <bool INV, typename V> __device__ __forceinline__ V mul_mj(V a) {
 // multiply by the twiddle w (forward) or conj(w) (inverse)
 template <bool INV, typename V> __device__ __forceinline__ V twmul(V a, V w) {
   return INV ? cmulc(a, w) : cmul(a, w);
+}
+// acc + twmul<INV>(a, w) as two fused multiply-adds per lane
+__device__ __forceinline__ float fmx(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmx(double a, double b, double c) { return __fma_rn(a, b, c); }
+template <bool INV, typename V> __device__ __forceinline__ V twmadd(V acc, V a, V w) {
+  return INV ? cmk<V>(fmx(a.y, w.y, fmx(a.x, w.x, acc.x)), fmx(-a.x, w.y, fmx(a.y, w.x, acc.y)))
+             : cmk<V>(fmx(-a.y, w.y, fmx(a.x, w.x, acc.x)), fmx(a.y, w.x, fmx(a.x, w.y, acc.y)));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -102,11 +133,17 @@ template <bool INV, typename V> __device__ __forceinline__ void dft2(V& a, V& b)
 }
 
 template <bool INV, typename V> __device__ __forceinline__ void dft4(V& a0, V& a1, V& a2, V& a3) {
-  V t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = mul_mj<INV>(csub(a1, a3));
+  V t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), d = csub(a1, a3);
   a0 = cadd(t0, t2);
   a2 = csub(t0, t2);
-  a1 = cadd(t1, t3);
-  a3 = csub(t1, t3);
+  // t1 +- (-+j) d lane by lane: a paired form would first have to swap d's lanes
+  if (INV) {
+    a1 = cmk<V>(t1.x - d.y, t1.y + d.x);
+    a3 = cmk<V>(t1.x + d.y, t1.y - d.x);
+  } else {
+    a1 = cmk<V>(t1.x + d.y, t1.y - d.x);
+    a3 = cmk<V>(t1.x - d.y, t1.y + d.x);
+  }
 }
 
 template <int R, bool INV, typename V> struct Dft;

@@ -462,7 +462,7 @@ struct FusedCta {
 #pragma unroll
       for (int i = 1; i < 16; ++i) {
         s0 = cadd(s0, v[i]);
-        s1 = cadd(s1, twmul<false>(v[i], tw16[i]));
+        s1 = twmadd<false>(s1, v[i], tw16[i]);
       }
       cp[0] = s0;
       cp[17] = s1;
@@ -489,7 +489,7 @@ struct FusedCta {
       const float2 b = (nz == 2) ? cp[17] : make_float2(0.f, 0.f);
       __syncwarp();
 #pragma unroll
-      for (int k = 0; k < 16; ++k) v[k] = cadd(a, twmul<true>(b, tw16[k]));
+      for (int k = 0; k < 16; ++k) v[k] = twmadd<true>(a, b, tw16[k]);
     } else {
 #pragma unroll
       for (int i = 0; i < 16; ++i) v[i] = (i < nz) ? cp[17 * i] : make_float2(0.f, 0.f);
@@ -520,7 +520,7 @@ struct FusedCta {
     if (nz == 2) {
       const float2 w = tw16[j];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) v[i] = cadd(xr[pad16(i)], twmul<true>(xr[pad16(i + 16)], w));
+      for (int i = 0; i < 16; ++i) v[i] = twmadd<true>(xr[pad16(i)], xr[pad16(i + 16)], w);
     } else if (nz == 1) {
 #pragma unroll
       for (int i = 0; i < 16; ++i) v[i] = xr[pad16(i)];
@@ -560,7 +560,7 @@ struct FusedCta {
     if (nz == 2) {
       const float2 w = tw16[j];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) v[i] = cadd(xr[pad16(i)], twmul<true>(xr[pad16(i + 16)], w));
+      for (int i = 0; i < 16; ++i) v[i] = twmadd<true>(xr[pad16(i)], xr[pad16(i + 16)], w);
     } else if (nz == 1) {
 #pragma unroll
       for (int i = 0; i < 16; ++i) v[i] = xr[pad16(i)];
@@ -1112,12 +1112,7 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE, SPARSE>::T,
       (void)save_t;
     }
     flag = was_live || (g.x * g.x + g.y * g.y > kap * kap);
-    // the sparse variant writes its result from the last epilogue (no dense grid to copy from)
-    if constexpr (SPARSE) {
-      if (last && !flag) c_out[(crank + C * row) * L1 + e] = make_float2(0.f, 0.f);
-    } else {
-      (void)last;
-    }
+    (void)last;
     return flag ? g : make_float2(0.f, 0.f);
   };
   // ext: a flagged element, in ascending o; returns z^(t+1), the next FFT input
@@ -1256,6 +1251,22 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE, SPARSE>::T,
         cta.band = 0;
         cta.sq_inv2_epi_fwd1([&](int row, int e, float2 g) { return update_admm(row, e, g, last, kap); }, !last, nz);
       } else {
+        if constexpr (SPARSE) {
+          // The sparse variant writes its result from the last epilogue (no dense grid to copy
+          // from): zeros at every position this thread updates there, then ext overwrites the
+          // flagged ones.  After a single iteration every position is flagged (all live in the
+          // first epilogue), and the warm start, read in that epilogue, stays untouched.
+          if (last && !first) {
+            for (int b = 0; b < S::PASSES; ++b) {
+              cta.band = b;
+              int row, j;
+              cta.sq_rowj(row, j);
+              float2* const o = c_out + (crank + C * row) * L1 + j;
+#pragma unroll
+              for (int i = 0; i < 16; ++i) o[16 * i] = make_float2(0.f, 0.f);
+            }
+          }
+        }
         epilogue_begin();
         for (int b = 0; b < S::PASSES; ++b) {
           cta.band = b;
