@@ -224,10 +224,10 @@ def run_reference(args, rank, world):
 
 # DRAM traffic of the fused kernel per instance, from one ncu capture of a small case of the
 # variant named here (profiles/fused_solve_256x256_fista_ncu_full.md: 152 instances x 200
-# iterations, dram__bytes_read.sum 177.25 MB + dram__bytes_write.sum 220.29 MB); the bytes do not
+# iterations, dram__bytes_read.sum 177.69 MB + dram__bytes_write.sum 219.43 MB); the bytes do not
 # grow with the iteration count past the dense first iterations, so they scale by instances
 FUSED_TRAFFIC_VARIANT = (8192, 1)  # (tile, sparse_state)
-FUSED_DRAM_BYTES_PER_INSTANCE = (177.252352e6 + 220.285696e6) / 152
+FUSED_DRAM_BYTES_PER_INSTANCE = (177.692160e6 + 219.427328e6) / 152
 
 
 def load_peaks():
@@ -598,7 +598,7 @@ def run_workload(args):
             c_net, t_net = timed(lambda: Lm.net_forward(net, y, scale, thresh))
         e_net = Lm.relative_errors(c_net, ref, n_eval, L)
         sweep = {}
-        for it in (16, 32, 48, 64):
+        for it in (16, 32, 48, 64, 128, 256):
             o, t = timed(lambda: plain(it))
             e = Lm.relative_errors(o, ref, n_eval, L)
             sweep[it] = {"ms": t, "rel_err_mean": e.mean().item()}
