@@ -408,6 +408,11 @@ def run_gpu(args, rank, world, local_rank):
                 "peak_note": f"FP32: {sm_count} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_max:.0f} MHz",
                 "frac_at_median_clock": (achieved / (sm_count * FP32_LANES_PER_SM * 2 * clock["sm_mhz"] * 1e6 / 1e12)
                                          if clock.get("sm_mhz") else None)}
+        # the derived FP32 peak confirmed on this GPU by a multiply-add microbenchmark (after the timed
+        # region; scalar FFMA and the paired f32x2 form the solver's butterflies use)
+        fma_rate = {"ffma": bccb.bccb_fp32_fma_rate(False), "ffma2": bccb.bccb_fp32_fma_rate(True)}
+        roof["peak_measured_fma_tflops"] = fma_rate
+        roof["frac_of_measured_fma"] = achieved / max(fma_rate.values())
         if args.traffic_bytes is not None:
             roof["traffic"] = args.traffic_bytes
         elif FUSED_TRAFFIC_VARIANT == (tile, sparse_state) and T > 0:

@@ -316,6 +316,16 @@ int bccb_destroy(bccb_solver_t s);
 int bccb_solve_noalloc(int M1, int M2, const uint8_t* mask_dev, int L1, int L2, int algo, double rho,
                        const void* y_dev, double lam, int lam_is_frac, int iters, void* c_out_dev,
                        void* cuda_stream);
+/* Measurement helper (no counterpart in the paper): the device's FP32 fused multiply-add
+ * rate in TFLOP/s, from event-timed launches on cuda_stream of a kernel whose threads run 16
+ * independent multiply-add chains for `iters` steps each, at full occupancy on every SM (best
+ * of three after a warm-up).  paired = 0: scalar fma.rn.f32; paired = 1: fma.rn.f32x2 (two
+ * lanes per instruction, the form the fused solver's butterflies use for their sums).  It
+ * confirms the FP32 peak (SMs x 128 lanes x 2 flop x clock) that the fused solver's roofline
+ * fraction is reported against.  Synchronises the stream; allocates nothing.  iters of about
+ * 20000 take a few milliseconds on a GB300.  Errors: INVALID_ARG (null tflops_out, iters < 1),
+ * CUDA. */
+int bccb_fp32_fma_rate(int paired, int iters, void* cuda_stream, double* tflops_out);
 const char* bccb_status_string(int status);
 /* Message for the solver's last failure ("" if none); s may be NULL for create errors. */
 const char* bccb_last_error(bccb_solver_t s);

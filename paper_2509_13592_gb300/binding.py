@@ -73,6 +73,7 @@ def _load():
     lib.bccb_batch_size.argtypes = [vp, P(i32)]
     lib.bccb_instance_shape.argtypes = [vp, i32, P(i32), P(i32), P(i32)]
     lib.bccb_destroy.argtypes = [vp]
+    lib.bccb_fp32_fma_rate.argtypes = [i32, i32, vp, P(dbl)]
     lib.bccb_status_string.argtypes = [i32]
     lib.bccb_status_string.restype = ctypes.c_char_p
     lib.bccb_last_error.argtypes = [vp]
@@ -81,7 +82,8 @@ def _load():
                  "bccb_batch_get", "bccb_create", "bccb_solve", "bccb_batch_size", "bccb_instance_shape",
                  "bccb_destroy", "bccb_set_timing", "bccb_last_timing", "bccb_batch_capture", "bccb_batch_replay",
                  "bccb_batch_tune", "bccb_batch_tile", "bccb_unrolled_fwd", "bccb_unrolled_bwd", "bccb_batch_peaks",
-                 "bccb_batch_set_method", "bccb_batch_create_gamma", "bccb_set_kkt_tol", "bccb_mu", "bccb_batch_status", "bccb_batch_variant"):
+                 "bccb_batch_set_method", "bccb_batch_create_gamma", "bccb_set_kkt_tol", "bccb_mu", "bccb_batch_status", "bccb_batch_variant",
+                 "bccb_fp32_fma_rate"):
         getattr(lib, name).restype = i32
     return lib
 
@@ -270,6 +272,13 @@ def bccb_last_timing(h: int):
     _raise(_lib.bccb_last_timing(h, ctypes.byref(f[0]), ctypes.byref(f[1]), ctypes.byref(f[2]),
                                  ctypes.byref(n)), h)
     return {"setup_ms": f[0].value, "iterate_ms": f[1].value, "check_ms": f[2].value, "launches": n.value}
+
+
+def bccb_fp32_fma_rate(paired: bool = False, iters: int = 20000, stream=None) -> float:
+    """Measured FP32 multiply-add rate of the current device in TFLOP/s (scalar, or paired f32x2)."""
+    out = ctypes.c_double(0.0)
+    _raise(_lib.bccb_fp32_fma_rate(1 if paired else 0, int(iters), _stream(stream), ctypes.byref(out)), None)
+    return out.value
 
 
 def bccb_batch_solve_host_ptr(h: int, y_host_ptr: int, iters: int, c_out_host_ptr: int, check: bool = True) -> None:

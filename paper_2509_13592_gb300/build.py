@@ -29,7 +29,7 @@ def _units():
     units = [("api", "api.cu", []), ("setup_fp64", "setup_fp64.cu", []),
              ("fused_dispatch", "fused_dispatch.cu", []), ("noalloc", "noalloc.cu", []),
              ("multipass", "multipass.cu", []), ("peaks", "peaks.cu", []),
-             ("dense", "dense.cu", [])]
+             ("dense", "dense.cu", []), ("fma_rate", "fma_rate.cu", [])]
     for l2 in L2_VALUES:
         units.append((f"fused_L2_{l2}", "fused_inst.cu", [f"-DBCCB_L2={l2}"]))
     return units
