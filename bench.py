@@ -546,11 +546,26 @@ def run_workload(args):
                              "nonzeros_z": int(np.count_nonzero(z)), "kkt": float(r["kkt"][0]),
                              "objective": float(r["objective"][0])}
             studies.append(row)
+        # the FP64 oracle on the host cores (Kronecker-factored products: the dense A would be 16 GiB),
+        # timed at 20 and 60 iterations and extrapolated to the study's length
+        K = oracle.KronDictionary(s.mask, s.M1, s.M2, s.L1, s.L2)
+        lam_o = 0.05 * float(np.abs(K.adjoint(s.y)).max())
+        t_cpu = {}
+        for n_it in (5, 20, 60):  # the first call warms the BLAS threads and caches
+            t0 = time.perf_counter()
+            oracle.admm_kron(K, s.y, lam_o, 1024.0, n_it)
+            t_cpu[n_it] = time.perf_counter() - t0
+        per_it = (t_cpu[60] - t_cpu[20]) / 40
+        cpu_oracle = {"kind": "oracle.admm_kron (FP64, products through the Kronecker factors of D)",
+                      "cores": os.cpu_count(), "s_per_iteration": per_it,
+                      "s_setup": max(t_cpu[20] - 20 * per_it, 0.0),
+                      "extrapolated_s_for_study": max(t_cpu[20] - 20 * per_it, 0.0) + T * per_it,
+                      "sample": "20 and 60 iterations timed after a warm-up call, extrapolated linearly to the study's length"}
         line = {"workload": f"1024x1024 grid, 64x64 array N=1024, 20 off-grid sources, 15 dB, lam=0.05||A^H y||_inf, "
                             f"ADMM {T} iterations, single snapshot; rho = 0.5 (stated) and rho = N",
                 "reference": "FP64 oracle (tests/golden/admm1024_rho*.txt): z^(T) in full, c^(T) on 1024 sampled "
                              "entries and in norm",
-                "studies": studies}
+                "studies": studies, "cpu_oracle": cpu_oracle}
     elif args.workload == "learned":
         # unrolled FISTA, 16 layers with learned per-layer step and threshold multipliers (fixed 32x32
         # array, N = 256, 256x256 grid), judged against 1000-iteration plain FISTA
@@ -689,6 +704,62 @@ def run_workload(args):
                 "unit": "instances/s", "ms_per_batch": ms, "peaks_per_instance_median": float(np.median(cnt)),
                 "bytes_read_per_instance_pass": 65536 * 8,
                 "cpu_oracle": {"ms_per_instance": cpu_s * 1e3, "cores": 1, "sample": "16 instances"}}
+    elif args.workload == "torchfft":
+        # Context only, outside the library: the same FISTA iteration written with torch.fft (cuFFT) on
+        # the same FP32 setup (q, Bt, mu, lam taken from the library's solver), against the fused solver
+        B, T = args.batch, args.iters
+        snaps = [synth.make_snapshot(20000 + i, 32, 32, 256, 256, 256, 8, 10.0) for i in range(B)]
+        insts = [dict(M1=q.M1, M2=q.M2, L1=q.L1, L2=q.L2, mask=q.mask, y=q.y, lam=0.05, lam_is_frac=True) for q in snaps]
+        (c_fused, _), t_fused, res = _solve_timed(bccb, torch, insts, "fista", T, reps=3, check=True)
+        solver = bccb.BatchSolver(insts, "fista")
+        y = torch.from_numpy(solver.y_host).cuda()
+        c = torch.zeros(solver.total_c, dtype=torch.complex64, device="cuda")
+        solver.solve(y, 1, c, check=False)
+        q = torch.empty(solver.total_c, dtype=torch.float32, device="cuda")
+        bt = torch.empty(solver.total_c, dtype=torch.complex64, device="cuda")
+        solver.get(2, q)
+        solver.get(3, bt)
+        r1 = solver.results()
+        solver.close()
+        kappa = torch.tensor(np.asarray(r1["mu"]) * np.asarray(r1["lam"]), dtype=torch.float32, device="cuda").view(B, 1, 1)
+        q, bt = q.view(B, 256, 256), bt.view(B, 256, 256)
+        tk, beta = 1.0, []
+        for _ in range(T):
+            tn = (1.0 + (1.0 + 4.0 * tk * tk) ** 0.5) / 2.0
+            beta.append((tk - 1.0) / tn)
+            tk = tn
+
+        def torch_fista():
+            z = torch.zeros(B, 256, 256, dtype=torch.complex64, device="cuda")
+            c_prev = torch.zeros_like(z)
+            for t in range(T):
+                g = torch.fft.ifft2(q * torch.fft.fft2(z) - bt, norm="forward")  # unnormalised inverse
+                u = z - g
+                mag = u.abs()
+                cn = u * torch.clamp(1.0 - kappa / torch.clamp(mag, min=1e-30), min=0.0)
+                z = cn + beta[t] * (cn - c_prev)
+                c_prev = cn
+            return c_prev
+
+        torch_fista()  # warm-up (cuFFT plans)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ts = []
+        for _ in range(3):
+            e0.record()
+            c_t = torch_fista()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        t_torch = statistics.median(ts)
+        ct = c_t.reshape(-1).cpu().numpy().astype(np.complex128)
+        cf = c_fused.astype(np.complex128)
+        line = {"workload": f"context only, not the library: FISTA x {T} on {B} snapshots of the 256x256 workload written "
+                            f"with torch.fft (cuFFT), FP32, on the library's q, Bt, mu and lam",
+                "value": B * T / (t_torch / 1e3), "unit": UNIT, "ms": t_torch,
+                "fused_value": B * T / (t_fused["iterate_ms"] / 1e3), "fused_iterate_ms": t_fused["iterate_ms"],
+                "fused_over_torch": t_torch / t_fused["iterate_ms"],
+                "rel_diff_vs_fused": float(np.linalg.norm(ct - cf) / np.linalg.norm(cf))}
     elif args.workload == "toeplitz":
         # element spacing 0.4 wavelength (gamma != 1/2): Toeplitz Gram, 2L1 x 2L2 circulant embedding
         B, T, g = min(args.batch, 1024), args.iters, (0.4, 0.4)
@@ -809,7 +880,7 @@ def main():
     ap.add_argument("--tune-cache", default=None, help="autotuner cache file (default: measure every run)")
     ap.add_argument("--workload", default="batched256",
                     choices=["batched256", "ragged", "precision1024", "single64", "table1", "peaks", "toeplitz",
-                             "learned"],
+                             "learned", "torchfft"],
                     help="batched256 is the benchmark metric; the others print their own line")
     ap.add_argument("--trials", type=int, default=3, help="trials per Table I cell (--workload table1)")
     ap.add_argument("--params", default=None, help="trained multipliers of the unrolled network (--workload learned)")
