@@ -1091,8 +1091,7 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE, SPARSE>::T,
   // quick: every output of the inverse transform (the thread's o-th).  Off the support the
   // state is exactly 0 and stays 0 while |G'| <= kappa: that element is finished here, touching
   // no memory.  Otherwise it is flagged and the (scaled) G' is kept for ext.
-  auto quick = [&](int row, int e, int o, float2 g, bool& flag, float sc, float kap, float2* save_t,
-                   bool last) -> float2 {
+  auto quick = [&](int row, int e, int o, float2 g, bool& flag, float sc, float kap, float2* save_t) -> float2 {
     if constexpr (BLOCK) {
       if (e >= in.bl1 || crank + C * row >= in.bl2) {  // outside the caller's block: stays 0
         flag = false;
@@ -1112,7 +1111,6 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE, SPARSE>::T,
       (void)save_t;
     }
     flag = was_live || (g.x * g.x + g.y * g.y > kap * kap);
-    (void)last;
     return flag ? g : make_float2(0.f, 0.f);
   };
   // ext: a flagged element, in ascending o; returns z^(t+1), the next FFT input
@@ -1271,7 +1269,7 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE, SPARSE>::T,
         for (int b = 0; b < S::PASSES; ++b) {
           cta.band = b;
           cta.sq_inv2_split_fwd1(
-              [&](int row, int e, int o, float2 g, bool& f) { return quick(row, e, o, g, f, sc, kap, save_t, last); },
+              [&](int row, int e, int o, float2 g, bool& f) { return quick(row, e, o, g, f, sc, kap, save_t); },
               [&](int row, int e, int o, float2 g) { return ext(row, e, o, g, beta, kap, last); }, !last, nz);
         }
         epilogue_end();
@@ -1309,7 +1307,7 @@ __global__ void __launch_bounds__(FusedShape<L1, L2, ADMM, TILE, SPARSE>::T,
             [&](int row, int e, float2 g) {
               bool f;
               const int o = ord++;
-              cta.work[row * P + pad16(e)] = quick(row, e, o, g, f, sc, kap, save_t, last);
+              cta.work[row * P + pad16(e)] = quick(row, e, o, g, f, sc, kap, save_t);
               if (f) flagged |= 1u << o;
             },
             kc);
