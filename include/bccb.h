@@ -21,10 +21,11 @@
  *   c      complex64, L1*L2 entries stored as an L2 x L1 row-major grid: entry
  *          l1 + l2*L1 is the amplitude at harmonics (f_{1,l1}, f_{2,l2}) with
  *          f_{i,l} = -1/2 + l/L_i (Section II-A: column l1 + l2 L1 of D).
- * Supported grids: L1, L2 powers of two in [16, 1024]; M1, M2 >= 1 (masks wider
- * than the grid fold, which the BCCB structure allows).  FP32 grids up to 256 x 256
- * run on chip (one thread-block cluster per instance); larger grids and the FP64
- * path run as two passes per iteration over L2-resident global memory.
+ * Supported grids: L1, L2 powers of two in [8, 1024]; M1, M2 >= 1 (masks wider
+ * than the grid fold, which the BCCB structure allows).  FP32 grids with both sides
+ * in [16, 256] run on chip (one thread-block cluster per instance); other grids (a
+ * side of 8, or above 256) and the FP64 path run as two passes per iteration over
+ * L2-resident global memory.
  *
  * Conventions
  *   * Every call returns a status (BCCB_OK = 0).  No exception crosses the ABI and

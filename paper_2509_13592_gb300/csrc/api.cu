@@ -24,6 +24,9 @@ namespace {
 thread_local std::string g_create_error;
 
 bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+// grids the fused on-chip kernel serves (FP32, sides 16 .. 256: its row and column stages are radix 16);
+// every other supported grid runs on the multi-pass solver, whose transforms take any power of two
+bool on_chip_grid(int prec, int L1, int L2) { return prec == BCCB_F32 && L1 >= 16 && L2 >= 16 && L1 <= 256 && L2 <= 256; }
 
 constexpr size_t kDenseMaxBytes = size_t(64) << 30;
 
@@ -163,16 +166,16 @@ int create_impl(bccb_solver_t* out, const bccb_inst_t* insts, int n, const uint8
       delete s;
       return fail(nullptr, BCCB_ERR_INVALID_ARG, "instance " + std::to_string(i) + ": bad M1/M2/offsets");
     }
-    if (!is_pow2(q.L1) || !is_pow2(q.L2) || q.L1 < 16 || q.L2 < 16 || q.L1 > 1024 || q.L2 > 1024) {
+    if (!is_pow2(q.L1) || !is_pow2(q.L2) || q.L1 < 8 || q.L2 < 8 || q.L1 > 1024 || q.L2 > 1024) {
       delete s;
       return fail(nullptr, BCCB_ERR_UNSUPPORTED,
-                  "instance " + std::to_string(i) + ": L1, L2 must be powers of two in [16, 1024]");
+                  "instance " + std::to_string(i) + ": L1, L2 must be powers of two in [8, 1024]");
     }
     if (!(q.lam >= 0.0)) {
       delete s;
       return fail(nullptr, BCCB_ERR_INVALID_ARG, "instance " + std::to_string(i) + ": lam must be >= 0");
     }
-    const bool on_chip = prec == BCCB_F32 && q.L1 <= 256 && q.L2 <= 256;
+    const bool on_chip = on_chip_grid(prec, q.L1, q.L2);
     if (on_chip && !bccb::fused_lookup(q.L1, q.L2, algo == BCCB_ADMM, 0, blk != nullptr)) {
       delete s;
       return fail(nullptr, BCCB_ERR_UNSUPPORTED, "no fused kernel for this grid");
@@ -250,7 +253,7 @@ int create_impl(bccb_solver_t* out, const bccb_inst_t* insts, int n, const uint8
     bccb::ShapeClass sc;
     sc.L1 = o.second.first;
     sc.L2 = o.second.second;
-    sc.multipass = !(prec == BCCB_F32 && sc.L1 <= 256 && sc.L2 <= 256);
+    sc.multipass = !on_chip_grid(prec, sc.L1, sc.L2);
     if (!sc.multipass)
       sc.entry = *bccb::fused_lookup(sc.L1, sc.L2, algo == BCCB_ADMM, 0, blk != nullptr);
     else

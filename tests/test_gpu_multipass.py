@@ -44,9 +44,24 @@ def test_fp64_path_matches_oracle_to_1e10(lib, algo, L1, L2):
         assert rel_err(run["aux"][0], ref["aux"]) <= 1e-10
 
 
+@pytest.mark.parametrize("algo", ["ista", "fista", "admm"])
+@pytest.mark.parametrize("L1,L2,M1,M2", [(8, 8, 12, 10), (8, 32, 12, 6), (64, 8, 10, 4), (8, 1024, 5, 40)])
+def test_side_of_8_runs_multipass(lib, algo, L1, L2, M1, M2):
+    """Grids with a side of 8 (below the fused kernel's radix-16 stages) run on the multi-pass
+    solver, FP32 to the parity bar and FP64 to 1e-10; masks wider than the grid fold (M_i > L_i)."""
+    s = _snap(9 * L1 + L2, M1, M2, max(4, (M1 * M2) // 3), L1, L2, K=2)
+    ref = oracle_run(s, algo, 150, rho=4.0)
+    run = gpu_run(lib, [s], [ref["lam"]], algo, 150, rho=4.0)
+    assert lib.bccb_batch_variant(run["solver"].handle, L1, L2) == (0, 0)  # not the on-chip kernel
+    assert_parity(run["c"][0], ref, what=f"{algo} {L1}x{L2} fp32")
+    run64 = gpu_run(lib, [s], [ref["lam"]], algo, 150, rho=4.0, prec="f64")
+    assert rel_err(run64["c"][0], ref["c"]) <= 1e-10
+    assert np.array_equal(np.abs(run64["c"][0]) > 0, np.abs(ref["c"]) > 0)
+
+
 def test_ragged_batch_mixing_on_chip_and_multipass(lib):
     snaps = [_snap(71, 8, 8, 20, 64, 64), _snap(72, 16, 4, 20, 512, 32), _snap(73, 8, 8, 20, 256, 256),
-             _snap(74, 4, 16, 20, 16, 1024)]
+             _snap(74, 4, 16, 20, 16, 1024), _snap(75, 6, 6, 12, 8, 16)]
     refs = [oracle_run(s, "fista", 100) for s in snaps]
     run = gpu_run(lib, snaps, [r["lam"] for r in refs], "fista", 100)
     for i, (c, r) in enumerate(zip(run["c"], refs)):

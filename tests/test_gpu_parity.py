@@ -386,7 +386,7 @@ def test_invalid_arguments(lib):
     s = _snap(46, 4, 4, 6, 16, 16)
     good = inst(s, 0.1)
     for bad, status in [(dict(good, L1=48), lib.ERR_UNSUPPORTED), (dict(good, L2=2048), lib.ERR_UNSUPPORTED),
-                        (dict(good, L1=8), lib.ERR_UNSUPPORTED),
+                        (dict(good, L1=4), lib.ERR_UNSUPPORTED),
                         (dict(good, mask=np.zeros(16, np.uint8)), lib.ERR_INVALID_ARG),
                         (dict(good, lam=-1.0), lib.ERR_INVALID_ARG)]:
         with pytest.raises(lib.BccbError) as e:
