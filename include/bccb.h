@@ -63,7 +63,9 @@ enum {
   BCCB_ERR_UNSUPPORTED = 2, /* grid size outside the supported set */
   BCCB_ERR_CUDA = 3,        /* a CUDA call failed; see bccb_last_error() */
   BCCB_ERR_KKT = 4,         /* result returned, but its FP64 KKT check failed (bccb_batch_solve) */
-  BCCB_ERR_TIMEOUT = 5      /* reserved: a bounded device wait expired */
+  BCCB_ERR_TIMEOUT = 5      /* reserved for a bounded device wait that expired; no kernel of this library
+                               waits on a flag or a peer (its waits are CTA and cluster barriers), so
+                               no call returns it */
 };
 
 /* One instance of a batch.  Offsets let the caller pack many instances into one
