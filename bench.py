@@ -501,7 +501,7 @@ def run_workload(args):
     torch.cuda.set_device(0)
     if args.workload == "ragged":
         B, T = args.batch, args.iters
-        snaps = synth.config_batch(3, B)
+        snaps = synth.workload_batch("ragged", B)
         insts = [dict(M1=s.M1, M2=s.M2, L1=s.L1, L2=s.L2, mask=s.mask, y=s.y, lam=0.1, lam_is_frac=True)
                  for s in snaps]
         _, t, _ = _solve_timed(bccb, torch, insts, "fista", T, check=True)
@@ -529,7 +529,7 @@ def run_workload(args):
         sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
         import make_admm1024 as golden
 
-        s = synth.config_snapshot(4, 0)
+        s = synth.workload_snapshot("admm1024", 0)
         s.y = s.y.astype(np.complex64).astype(np.complex128)  # the measurements the reference was given
         inst = [dict(M1=s.M1, M2=s.M2, L1=s.L1, L2=s.L2, mask=s.mask, y=s.y, lam=0.05, lam_is_frac=True)]
         T = golden.ITERS
@@ -801,7 +801,7 @@ def run_workload(args):
                 "cpu_oracle": {"value": cpu, "unit": "instance-iterations/s", "cores": os.cpu_count(),
                                "sample": "2 snapshots x 100 FISTA iterations, dense FP64 oracle incl. setup"}}
     elif args.workload == "single64":
-        s = synth.config_snapshot(1, 0)
+        s = synth.workload_snapshot("fista64", 0)
         inst = [dict(M1=s.M1, M2=s.M2, L1=s.L1, L2=s.L2, mask=s.mask, y=s.y, lam=0.1, lam_is_frac=True)]
         _, t, _ = _solve_timed(bccb, torch, inst, "fista", 500, reps=5, check=True)
         per_it_s = t["iterate_ms"] / 500 / 1e3

@@ -34,9 +34,9 @@ __all__ = [
     "element_positions",
     "on_grid_frequencies",
     "make_snapshot",
-    "config_snapshot",
-    "config_batch",
-    "CONFIGS",
+    "workload_snapshot",
+    "workload_batch",
+    "WORKLOADS",
 ]
 
 
@@ -144,50 +144,50 @@ def make_snapshot(
 
 
 # --------------------------------------------------------------------------------------------
-# Named workloads.  Seeds follow seed = 1000*config + instance.
+# Named workloads.  Each has a fixed seed base; instance i of a single-snapshot workload is drawn
+# with seed base + i.
 # --------------------------------------------------------------------------------------------
-CONFIGS = {
+WORKLOADS = {
     # Plain FISTA, 16x16 array, N=64, 64x64 grid, 3 on-grid unit sources, 20 dB, 500 iterations.
-    1: dict(M1=16, M2=16, N=64, L1=64, L2=64, K=3, snr_db=20.0, on_grid=True, unit_amplitude=True,
-            lam_frac=0.1, iters=500),
+    "fista64": dict(seed=1000, M1=16, M2=16, N=64, L1=64, L2=64, K=3, snr_db=20.0, on_grid=True,
+                    unit_amplitude=True, lam_frac=0.1, iters=500),
     # ISTA / FISTA / ADMM(rho=1), 32x32 array, N=256, 256x256 grid, 8 off-grid CN(0,1) sources, 10 dB.
-    2: dict(M1=32, M2=32, N=256, L1=256, L2=256, K=8, snr_db=10.0, on_grid=False, unit_amplitude=False,
-            lam_frac=0.05, iters=1000, rho=1.0),
+    "solve256": dict(seed=2000, M1=32, M2=32, N=256, L1=256, L2=256, K=8, snr_db=10.0, on_grid=False,
+                     unit_amplitude=False, lam_frac=0.05, iters=1000, rho=1.0),
     # 64x64 array, N=1024, 1024x1024 grid, 20 off-grid sources, 15 dB, ADMM rho=0.5, 2000 iterations.
-    4: dict(M1=64, M2=64, N=1024, L1=1024, L2=1024, K=20, snr_db=15.0, on_grid=False,
-            unit_amplitude=False, lam_frac=0.05, iters=2000, rho=0.5),
+    "admm1024": dict(seed=4000, M1=64, M2=64, N=1024, L1=1024, L2=1024, K=20, snr_db=15.0, on_grid=False,
+                     unit_amplitude=False, lam_frac=0.05, iters=2000, rho=0.5),
 }
 
 
-def config_snapshot(config: int, instance: int = 0, **overrides) -> Snapshot:
-    """One instance of a single-snapshot workload (configs 1, 2, 4)."""
-    p = dict(CONFIGS[config])
+def workload_snapshot(name: str, instance: int = 0, **overrides) -> Snapshot:
+    """Instance `instance` of a single-snapshot workload of WORKLOADS."""
+    p = dict(WORKLOADS[name])
     p.update(overrides)
     return make_snapshot(
-        1000 * config + instance,
+        p["seed"] + instance,
         p["M1"], p["M2"], p["N"], p["L1"], p["L2"], p["K"], p["snr_db"],
         on_grid=p["on_grid"], unit_amplitude=p["unit_amplitude"], lam_frac=p["lam_frac"],
     )
 
 
-def config_batch(config: int, count: int, first: int = 0, L_choices=(64, 128, 256),
-                 fixed_mask_seed: Optional[int] = None, L: Optional[int] = None) -> List[Snapshot]:
+def workload_batch(name: str, count: int, first: int = 0, L_choices=(64, 128, 256),
+                   fixed_mask_seed: Optional[int] = None, L: Optional[int] = None) -> List[Snapshot]:
     """Batched workloads.
 
-    config 3: per instance L1, L2 iid uniform on ``L_choices``, M_i = L_i/4, N =
-    round(0.25*M1*M2) random elements, K ~ U{1..10} off-grid, SNR ~ U[0, 30] dB.
+    "ragged": per instance L1, L2 iid uniform on ``L_choices``, M_i = L_i/4, N =
+    round(0.25*M1*M2) random elements, K ~ U{1..10} off-grid, SNR ~ U[0, 30] dB
+    (instance i from seed 3000 + i).  ``L`` forces a square L x L grid.
 
-    config 5: fixed 32x32 array with N=256 (mask from ``fixed_mask_seed``,
-    default 5000), 256x256 grid, K ~ U{1..8} off-grid, SNR ~ U[0, 30] dB.
+    "learned": fixed 32x32 array with N=256 (mask from ``fixed_mask_seed``, default
+    5000), 256x256 grid, K ~ U{1..8} off-grid, SNR ~ U[0, 30] dB (instance i from seed
+    5001 + i).
 
-    config 2 (batched form): every instance drawn like the single-snapshot
-    config 2 (own mask, 8 sources, 10 dB) with seed 2000 + instance.
-
-    ``L`` forces a square L x L grid for config 3 (used for the homogeneous
-    256 x 256 batch).
+    "solve256": every instance drawn like the single-snapshot workload (own mask,
+    8 sources, 10 dB) with seed 2000 + instance.
     """
     out: List[Snapshot] = []
-    if config == 3:
+    if name == "ragged":
         for i in range(first, first + count):
             rng = np.random.Generator(np.random.PCG64(3000 + i))
             if L is None:
@@ -201,7 +201,7 @@ def config_batch(config: int, count: int, first: int = 0, L_choices=(64, 128, 25
             snr = float(rng.uniform(0.0, 30.0))
             sub = int(rng.integers(0, 2**62))
             out.append(make_snapshot(sub, M1, M2, N, L1, L2, K, snr, lam_frac=0.1))
-    elif config == 5:
+    elif name == "learned":
         mseed = 5000 if fixed_mask_seed is None else fixed_mask_seed
         mask = make_mask(np.random.Generator(np.random.PCG64(mseed)), 32, 32, 256)
         for i in range(first, first + count):
@@ -210,11 +210,11 @@ def config_batch(config: int, count: int, first: int = 0, L_choices=(64, 128, 25
             snr = float(rng.uniform(0.0, 30.0))
             sub = int(rng.integers(0, 2**62))
             out.append(make_snapshot(sub, 32, 32, 256, 256, 256, K, snr, mask=mask, lam_frac=0.05))
-    elif config == 2:
+    elif name == "solve256":
         for i in range(first, first + count):
-            out.append(config_snapshot(2, i))
+            out.append(workload_snapshot("solve256", i))
     else:
-        raise ValueError("batched configs are 2, 3 and 5")
+        raise ValueError("batched workloads are 'ragged', 'learned' and 'solve256'")
     return out
 
 

@@ -1,7 +1,7 @@
 """Writes the FP64 reference of the 1024 x 1024 ADMM precision study (tests/golden/admm1024_rho*.txt).
 
 Workload: 64 x 64 half-wavelength array, N = 1024 random elements, L1 = L2 = 1024, K = 20
-off-grid sources, 15 dB (synth.config_snapshot(4, 0), seed 4000), lam = 0.05 ||A^H y||_inf,
+off-grid sources, 15 dB (synth.workload_snapshot("admm1024", 0), seed 4000), lam = 0.05 ||A^H y||_inf,
 ADMM (eq:admm) for 2000 iterations at rho = 0.5 (the stated value) and rho = N = 1024 (a
 well-scaled one).  The measurements are the complex64-rounded y, as the GPU paths receive
 them.  Only oracle/ computes: oracle.admm_kron, the dense ADMM with the products taken through
@@ -68,7 +68,7 @@ def errors(z, c, ref):
 def reference(rho):
     import oracle
 
-    s = synth.config_snapshot(4, 0)
+    s = synth.workload_snapshot("admm1024", 0)
     y = s.y.astype(np.complex64).astype(np.complex128)
     K = oracle.KronDictionary(s.mask, s.M1, s.M2, s.L1, s.L2)
     lam = LAM_FRAC * float(np.abs(K.adjoint(y)).max())
@@ -83,7 +83,7 @@ def write(rho, path):
     idx = np.sort(np.random.Generator(np.random.PCG64(4242)).choice(c.size, SAMPLES, replace=False))
     with open(path, "w") as f:
         f.write(f"# FP64 ADMM reference, 1024x1024 precision study, rho = {rho!r}; written by make_admm1024.py\n")
-        f.write(f"# seed 4000 (synth.config_snapshot(4, 0)), iters {ITERS}, lam = {LAM_FRAC} ||A^H y||_inf\n")
+        f.write(f"# seed 4000 (synth.workload_snapshot('admm1024', 0)), iters {ITERS}, lam = {LAM_FRAC} ||A^H y||_inf\n")
         f.write(f"lam {float(lam)!r}\nrho {float(rho)!r}\niters {ITERS}\n")
         for name, x in (("z", z), ("c", c), ("v", v)):
             f.write(f"norm_{name} {float(np.linalg.norm(x))!r}\n")

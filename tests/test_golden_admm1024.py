@@ -19,7 +19,7 @@ import make_admm1024 as golden  # noqa: E402
 @pytest.mark.parametrize("tag,rho", [("0p5", 0.5), ("1024", 1024.0)])
 def test_reference_header_and_samples(tag, rho):
     ref = golden.read(tag)
-    s = synth.config_snapshot(4, 0)
+    s = synth.workload_snapshot("admm1024", 0)
     y = s.y.astype(np.complex64).astype(np.complex128)
     K = oracle.KronDictionary(s.mask, s.M1, s.M2, s.L1, s.L2)
     assert ref["lam"] == pytest.approx(0.05 * np.abs(K.adjoint(y)).max(), rel=1e-13)

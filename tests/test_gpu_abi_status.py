@@ -24,7 +24,7 @@ def test_mu_before_and_after_a_solve(lib):
     solve and equal to the value the solve reports."""
     import torch
 
-    snaps = [synth.config_snapshot(1, 0), synth.make_snapshot(91, 20, 6, 50, 16, 32, 2, 10.0)]  # 2nd folds
+    snaps = [synth.workload_snapshot("fista64", 0), synth.make_snapshot(91, 20, 6, 50, 16, 32, 2, 10.0)]  # 2nd folds
     solver = lib.BatchSolver([inst(s, 0.1, True) for s in snaps], "fista")
     mu = solver.mu()
     for i, s in enumerate(snaps):
@@ -40,7 +40,7 @@ def test_create_with_fp64_precision(lib):
     """bccb_create(..., prec = BCCB_F64, ...) solves in complex128 to the FP64 path's bar."""
     import torch
 
-    s = synth.config_snapshot(1, 0)
+    s = synth.workload_snapshot("fista64", 0)
     h = lib.bccb_create(s.M1, s.M2, s.mask, s.L1, s.L2, lib.FISTA, 1.0, None, lib.F64)
     try:
         y = torch.from_numpy(s.y.astype(np.complex128)).cuda()
@@ -58,7 +58,7 @@ def test_kkt_status_per_instance(lib):
     tolerance; the call returns BCCB_ERR_KKT and still writes every result."""
     import torch
 
-    snaps = [synth.config_snapshot(1, i) for i in range(4)]
+    snaps = [synth.workload_snapshot("fista64", i) for i in range(4)]
     lams = [0.1 * oracle.lambda_max(oracle.dictionary(s.mask, s.M1, s.M2, s.L1, s.L2), s.y) for s in snaps]
     solver = lib.BatchSolver([inst(s, l) for s, l in zip(snaps, lams)], "fista")
     y = torch.from_numpy(solver.y_host).cuda()
@@ -89,7 +89,7 @@ def test_kkt_status_per_instance(lib):
 def test_status_refused_inside_capture_and_without_check(lib):
     import torch
 
-    s = synth.config_snapshot(1, 0)
+    s = synth.workload_snapshot("fista64", 0)
     stream = torch.cuda.Stream()
     solver = lib.BatchSolver([inst(s, 0.1, True)], "fista", stream=stream)
     y = torch.from_numpy(solver.y_host).cuda()
@@ -110,7 +110,7 @@ def test_status_refused_inside_capture_and_without_check(lib):
 def test_unrolled_batch_argument_checked(lib):
     import torch
 
-    s = synth.config_snapshot(1, 0)
+    s = synth.workload_snapshot("fista64", 0)
     solver = lib.BatchSolver([inst(s, 0.1, True)] * 2, "fista")
     y = torch.from_numpy(solver.y_host).cuda()
     c = torch.zeros(solver.total_c, dtype=torch.complex64, device="cuda")

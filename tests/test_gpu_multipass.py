@@ -74,7 +74,7 @@ def test_1024x1024_two_ista_iterations_sampled(lib, prec):
     iterations from zero, checked at sampled grid cells.  The oracle forms b = A^H y from the
     Kronecker factors of D, c1 = S(mu b) exactly, and c2 = S(c1 - mu A^H A c1 + mu b) at the sampled cells from the
     columns on c1's support."""
-    s = synth.config_snapshot(4, 0)
+    s = synth.workload_snapshot("admm1024", 0)
     L = s.L1 * s.L2
     b = oracle.adjoint_measurements_kron(s.mask, s.M1, s.M2, s.L1, s.L2, s.y)
     mu = 1.0 / L  # sigma_max(A)^2 = L1 L2: rows of the partial DFT are orthogonal (M_i <= L_i)
@@ -100,7 +100,7 @@ def test_1024x1024_admm_fp32_vs_fp64_paths(lib):
     """Precision study at full size (64 x 64 array, N = 1024, 1024 x 1024 grid, 20 off-grid sources,
     15 dB, ADMM rho = 0.5): the FP32 path against the FP64 path after 300 iterations, both returned
     iterates and the FP64 KKT residuals."""
-    s = synth.config_snapshot(4, 0)
+    s = synth.workload_snapshot("admm1024", 0)
     # lam as a fraction of ||A^H y||_inf is applied on the device by both paths
     r32 = gpu_run_frac(lib, s, "f32")
     r64 = gpu_run_frac(lib, s, "f64")

@@ -72,7 +72,7 @@ def test_shared_mask_batch_shares_lambda(lib):
 
 
 def test_lambda_fraction_of_lmax(lib):
-    s = synth.config_snapshot(1, 3)
+    s = synth.workload_snapshot("fista64", 3)
     A = oracle.dictionary(s.mask, s.M1, s.M2, s.L1, s.L2)
     run = gpu_run_frac(lib, s, 0.1)
     assert abs(run["res"]["lam"][0] / (0.1 * oracle.lambda_max(A, s.y)) - 1.0) <= 1e-6
@@ -95,7 +95,7 @@ def gpu_run_frac(lib, s, frac):
 
 def test_fista_64x64_500_iterations(lib):
     """Plain FISTA, 16x16 array, N=64, 64x64 grid, 3 on-grid sources, 20 dB, 500 iterations."""
-    s = synth.config_snapshot(1, 0)
+    s = synth.workload_snapshot("fista64", 0)
     ref = oracle_run(s, "fista", 500)
     run = gpu_run(lib, [s], [ref["lam"]], "fista", 500)
     assert_parity(run["c"][0], ref, what="fista 64x64")
@@ -106,7 +106,7 @@ def test_fista_64x64_500_iterations(lib):
 def test_256x256_1000_iterations(lib, algo, rho):
     """32x32 array, N=256, 256x256 grid, 8 off-grid sources, 10 dB, 1000 iterations (ADMM with
     rho = 1 as specified, and with rho = 256 = N, where ADMM actually moves z off 0)."""
-    s = synth.config_snapshot(2, 0)
+    s = synth.workload_snapshot("solve256", 0)
     ref = oracle_run(s, algo, 1000, rho=rho)
     run = gpu_run(lib, [s], [ref["lam"]], algo, 1000, rho=rho)
     assert_parity(run["c"][0], ref, what=f"{algo} 256x256 rho={rho}")
@@ -180,7 +180,7 @@ def test_middle_stage_row_support(lib, algo, M2, tmp_path):
 
 
 def test_ragged_batch_matches_oracle(lib):
-    snaps = synth.config_batch(3, 10)
+    snaps = synth.workload_batch("ragged", 10)
     refs = [oracle_run(s, "fista", 200) for s in snaps]
     run = gpu_run(lib, snaps, [r["lam"] for r in refs], "fista", 200)
     for i, (c, r) in enumerate(zip(run["c"], refs)):
@@ -208,7 +208,7 @@ def test_both_tiles_match_oracle(lib, algo, tmp_path):
     oracle's iterates; the tile is forced through the tuner's cache file."""
     import torch
 
-    snaps = [synth.config_snapshot(2, 3), synth.make_snapshot(91, 16, 32, 128, 64, 128, 3, 15.0),
+    snaps = [synth.workload_snapshot("solve256", 3), synth.make_snapshot(91, 16, 32, 128, 64, 128, 3, 15.0),
              synth.make_snapshot(92, 32, 16, 128, 256, 64, 3, 15.0)]
     refs = [oracle_run(s, algo, 120, rho=8.0) for s in snaps]
     for tile in (8192, 4096):
@@ -228,7 +228,7 @@ def test_both_tiles_match_oracle(lib, algo, tmp_path):
 def test_tuner_measures_and_caches(lib, tmp_path):
     import torch
 
-    snaps = synth.config_batch(3, 12, first=40)
+    snaps = synth.workload_batch("ragged", 12, first=40)
     solver = lib.BatchSolver([inst(s, 0.1, lam_is_frac=True) for s in snaps], "fista")
     y = torch.from_numpy(solver.y_host).cuda()
     cache = tmp_path / "tiles.txt"
@@ -243,7 +243,7 @@ def test_tuner_measures_and_caches(lib, tmp_path):
 def test_graph_replay_matches_direct_solve(lib):
     import torch
 
-    snaps = synth.config_batch(3, 9, first=60)
+    snaps = synth.workload_batch("ragged", 9, first=60)
     solver = lib.BatchSolver([inst(s, 0.1, lam_is_frac=True) for s in snaps], "fista",
                              stream=torch.cuda.Stream())
     y = torch.from_numpy(solver.y_host).cuda()
@@ -316,7 +316,7 @@ def test_one_iteration_and_warm_start(lib):
 
 
 def test_host_entry_point_matches_device(lib):
-    snaps = synth.config_batch(3, 3, first=20)
+    snaps = synth.workload_batch("ragged", 3, first=20)
     lams = [0.1 * oracle.lambda_max(oracle.dictionary(s.mask, s.M1, s.M2, s.L1, s.L2), s.y) for s in snaps]
     dev = gpu_run(lib, snaps, lams, "fista", 50)
     solver = dev["solver"]

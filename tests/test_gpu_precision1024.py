@@ -27,7 +27,7 @@ ITERS = golden.ITERS
 def run_gpu(lib, rho, prec):
     import torch
 
-    s = synth.config_snapshot(4, 0)
+    s = synth.workload_snapshot("admm1024", 0)
     s.y = s.y.astype(np.complex64).astype(np.complex128)  # the values the reference was given
     solver = lib.BatchSolver([inst(s, 0.05, lam_is_frac=True)], "admm", rho, prec=prec)
     cdt = torch.complex128 if prec == "f64" else torch.complex64

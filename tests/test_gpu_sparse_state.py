@@ -46,7 +46,7 @@ def _solve(lib, snaps, lams, algo, iters, sparse, tmp_path, c0=None, frac=False)
 @pytest.mark.parametrize("algo", ["fista", "ista"])
 def test_sparse_state_matches_oracle_and_dense_tile(lib, algo, tmp_path):
     # rows of 256 with 256, 128, 64 and 32 rows (8, 4, 2 and 1 CTAs per instance)
-    snaps = [synth.config_snapshot(2, 5), synth.make_snapshot(93, 32, 16, 200, 256, 128, 4, 12.0),
+    snaps = [synth.workload_snapshot("solve256", 5), synth.make_snapshot(93, 32, 16, 200, 256, 128, 4, 12.0),
              synth.make_snapshot(94, 24, 8, 90, 256, 64, 3, 15.0), synth.make_snapshot(95, 20, 6, 60, 256, 32, 2, 20.0)]
     iters = 300
     refs = [oracle_run(s, algo, iters) for s in snaps]
@@ -63,7 +63,7 @@ def test_sparse_state_matches_oracle_and_dense_tile(lib, algo, tmp_path):
 def test_sparse_state_warm_start_and_one_iteration(lib, tmp_path):
     """A warm start with a dense c0 (every position live in the first iteration, beyond the two
     slots of each thread), and a single iteration (the result written by the first epilogue)."""
-    s = synth.config_snapshot(2, 6)
+    s = synth.workload_snapshot("solve256", 6)
     ref = oracle_run(s, "fista", 40)
     rng = np.random.default_rng(3)
     c0 = (rng.standard_normal(65536) + 1j * rng.standard_normal(65536)) * 1e-3

@@ -256,7 +256,7 @@ def test_shift_equivariance():
 
 def test_noiseless_on_grid_sources_are_the_largest_peaks():
     """Config-1-shaped problem without noise: the K largest |c| sit on the true grid cells."""
-    s = synth.config_snapshot(1, 0, snr_db=None)
+    s = synth.workload_snapshot("fista64", 0, snr_db=None)
     A = oracle.dictionary(s.mask, s.M1, s.M2, s.L1, s.L2)
     lam = 0.1 * oracle.lambda_max(A, s.y)
     c = oracle.fista(A, s.y, lam, 500)

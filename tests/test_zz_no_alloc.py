@@ -42,7 +42,7 @@ def _noalloc(lib, f, s, algo, lam, iters, rho, lam_is_frac=0, mask=None):
 
 def test_noalloc_matches_ordinary_entry_point_on_two_calls_in_a_row(lib):
     f = _entry(lib)
-    s1 = synth.config_snapshot(2, 1)  # 32x32 array, N=256, 256x256 grid
+    s1 = synth.workload_snapshot("solve256", 1)  # 32x32 array, N=256, 256x256 grid
     s2 = synth.make_snapshot(77, 16, 32, 120, 64, 128, 4, 12.0)
     s3 = synth.make_snapshot(78, 12, 8, 40, 32, 64, 3, 15.0)
     # (snapshot, algorithm, iterations, rho, lam given as a fraction of ||A^H y||_inf)
@@ -64,7 +64,7 @@ def test_noalloc_against_the_oracle(lib):
     from gpu_util import assert_parity, oracle_run
 
     f = _entry(lib)
-    s = synth.config_snapshot(1, 0)  # 16x16 array, N = 64, 64x64 grid, 3 on-grid sources
+    s = synth.workload_snapshot("fista64", 0)  # 16x16 array, N = 64, 64x64 grid, 3 on-grid sources
     ref = oracle_run(s, "fista", 500)
     got = _noalloc(lib, f, s, "fista", ref["lam"], 500, 1.0)
     assert_parity(got, ref, what="noalloc FISTA 64x64")
