@@ -224,10 +224,10 @@ def run_reference(args, rank, world):
 
 # DRAM traffic of the fused kernel per instance, from one ncu capture of a small case of the
 # variant named here (152 instances x 200 iterations of the 256x256 workload: dram__bytes_read.sum
-# 177.69 MB + dram__bytes_write.sum 219.43 MB); the bytes do not grow with the iteration count past
+# 177.97 MB + dram__bytes_write.sum 219.73 MB); the bytes do not grow with the iteration count past
 # the dense first iterations, so they scale by instances
 FUSED_TRAFFIC_VARIANT = (8192, 1)  # (tile, sparse_state)
-FUSED_DRAM_BYTES_PER_INSTANCE = (177.692160e6 + 219.427328e6) / 152
+FUSED_DRAM_BYTES_PER_INSTANCE = (177.968128e6 + 219.734784e6) / 152
 
 
 def load_peaks():
