@@ -20,3 +20,11 @@ def test_cpu_fft_leg_matches_dense_oracle():
         assert np.count_nonzero(ref) > 0
         err = np.linalg.norm(c[i].reshape(-1) - ref) / np.linalg.norm(ref)
         assert err <= 1e-12, f"instance {i}: {err:.2e}"
+
+
+def test_algorithmic_flops_per_instance_iteration():
+    """The roofline's unit: a forward and an inverse 2D FFT at 5 L log2 L flops each plus 18 L
+    pointwise flops, L = L1 L2 (11.67 M on the 256 x 256 grid)."""
+    assert bench.flops_per_inst_iter(256, 256) == (10 * 16 + 18) * 65536
+    assert bench.flops_per_inst_iter(64, 64) == (10 * 12 + 18) * 4096
+    assert bench.flops_per_inst_iter(1024, 1024) == (10 * 20 + 18) * 2**20
